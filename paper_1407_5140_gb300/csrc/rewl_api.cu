@@ -1,0 +1,983 @@
+// rewl_api.cu -- host side of the C ABI declared in include/rewl.h.
+//
+// Builds the geometry of each instance (bins, windows, realisable energies),
+// owns the device state, plans the sweep launches (one per size class, run
+// concurrently on forked streams; windows per block and lanes per walker from
+// the autotuner), captures the sweep/exchange cycle in a CUDA graph, and joins
+// the ln g pieces on the host for rewl_get_dos (Sec. II B).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "rewl.h"
+#include "rewl_internal.h"
+
+using namespace rewl;
+typedef unsigned long long ull;
+
+struct HostInst {
+    rewl_instance desc;
+    InstDev dev;
+    std::vector<int> lo;
+    std::vector<uint8_t> reach;
+    std::vector<int> n_reach;
+};
+
+struct SizeClass {
+    int model, L, q, w, m, lat_words, N;
+    std::vector<int> insts;
+    std::vector<WorkItem> items;
+    WorkItem *d_items = nullptr;
+    SweepLaunch sl{};
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
+struct rewl_ctx {
+    std::vector<HostInst> inst;
+    int n_win = 0, n_slots = 0;
+    long long n_lng = 0, n_lat = 0, n_reach_bytes = 0;
+    // device buffers
+    InstDev *d_inst = nullptr;
+    int32_t *d_lo = nullptr, *d_nreach = nullptr, *d_stage = nullptr;
+    uint8_t *d_conv = nullptr;
+    int64_t *d_conv_sweep = nullptr;
+    ull *d_ex_prop = nullptr, *d_ex_acc = nullptr;
+    int32_t *d_cfg = nullptr, *d_E = nullptr, *d_bin = nullptr, *d_replica = nullptr, *d_slot_inst = nullptr;
+    ull *d_draw = nullptr, *d_nacc = nullptr;
+    uint8_t *d_latch = nullptr;
+    long long *d_lng = nullptr;
+    uint32_t *d_H = nullptr, *d_lat = nullptr;
+    uint8_t *d_reach = nullptr;
+    ull *d_counters = nullptr;
+    int *d_error = nullptr;
+    ExTask *d_ex0 = nullptr, *d_ex1 = nullptr;
+    int n_ex0 = 0, n_ex1 = 0;
+    DevState st{};
+    std::vector<SizeClass> classes;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaEvent_t fork = nullptr;
+    long check_every = 1;
+    long max_sweeps_per_launch = 1L << 30;
+    int force_lanes = 0, force_wpc = 0;
+    bool planned = false;
+    cudaGraphExec_t graph = nullptr;
+    long graph_sweeps = -1;
+    long graph_launches = 0;
+    long launches = 0;
+    int failed = 0;
+    std::string err;
+};
+
+static thread_local std::string g_create_error;
+
+static rewl_status fail(rewl_ctx *c, rewl_status s, const std::string &msg)
+{
+    if (c) {
+        if (!c->failed) c->err = msg;
+        if (s == REWL_ECUDA || s == REWL_EDEVICE) c->failed = 1;
+    } else {
+        g_create_error = msg;
+    }
+    return s;
+}
+
+#define CK(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(ctx, REWL_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// geometry (Sec. II A, Fig. 1)
+// ---------------------------------------------------------------------------
+static bool realisable(int model, int q, long long N, long long E)
+{
+    const long long off = E + 2 * N;
+    if (model == REWL_ISING) {
+        if (off < 0 || off > 4 * N || off % 4) return false;
+        const long long u = off / 4;  // unsatisfied bonds / 2
+        return u != 1 && u != N - 1;
+    }
+    if (off < 0 || off > 2 * N) return false;
+    if (q == 2) return off % 2 == 0 && off != 2 && off != 2 * N - 2;
+    return !(off == 1 || off == 2 || off == 3 || off == 5);
+}
+
+static rewl_status build_instance(const rewl_instance &d, HostInst &hi, std::string &why)
+{
+    char buf[256];
+    if (d.model != REWL_ISING && d.model != REWL_POTTS) { why = "model must be REWL_ISING or REWL_POTTS"; return REWL_EINVAL; }
+    if (d.L < 4 || d.L > 128 || d.L % 2) { why = "L must be even, 4 <= L <= 128"; return REWL_EINVAL; }
+    const int q = d.model == REWL_ISING ? 2 : d.q;
+    if (d.model == REWL_POTTS && (q < 2 || q > 127)) { why = "q must be in 2..127"; return REWL_EINVAL; }
+    if (d.n_windows < 1 || d.n_windows > 65535) { why = "n_windows must be in 1..65535"; return REWL_EINVAL; }
+    if (d.walkers_per_window < 1 || d.walkers_per_window > 1024) { why = "walkers_per_window must be in 1..1024"; return REWL_EINVAL; }
+    if (!(d.overlap >= 0.0 && d.overlap < 1.0)) { why = "overlap must be in [0, 1)"; return REWL_EINVAL; }
+    if (!(d.flatness > 0.0 && d.flatness <= 1.0)) { why = "flatness must be in (0, 1]"; return REWL_EINVAL; }
+    if (!(d.ln_f_final >= std::ldexp(1.0, -32) && d.ln_f_final <= 1.0)) { why = "ln_f_final must be in [2^-32, 1]"; return REWL_EINVAL; }
+    const long long N = (long long)d.L * d.L;
+    const int step = d.model == REWL_ISING ? 4 : 1;
+    const long long emin_m = -2 * N, emax_m = d.model == REWL_ISING ? 2 * N : 0;
+    if (d.e_min < emin_m || d.e_max > emax_m || d.e_min >= d.e_max || (d.e_min - emin_m) % step ||
+        (d.e_max - emin_m) % step) {
+        snprintf(buf, sizeof buf, "energy range [%lld, %lld] must lie in [%lld, %lld] on the bin grid (step %d)",
+                 (long long)d.e_min, (long long)d.e_max, emin_m, emax_m, step);
+        why = buf;
+        return REWL_EINVAL;
+    }
+    const int B = (int)((d.e_max - d.e_min) / step) + 1;
+    const int h = d.n_windows;
+    // equal widths: consecutive windows start (1 - o) w apart and cover B bins
+    const double span = 1.0 + (double)(h - 1) * (1.0 - d.overlap);
+    int w = (int)std::ceil((double)B / span);
+    if (w > B) w = B;
+    const int maxdb = d.model == REWL_ISING ? 2 : 4;
+    if (w < 2 * maxdb + 1) { why = "windows narrower than 2 * (largest bin change) + 1"; return REWL_EINVAL; }
+    hi.desc = d;
+    hi.lo.resize(h);
+    for (int i = 0; i < h; ++i) hi.lo[i] = h == 1 ? 0 : (int)(((long long)i * (B - w)) / (h - 1));
+    hi.reach.resize(B);
+    for (int b = 0; b < B; ++b) hi.reach[b] = realisable(d.model, q, N, d.e_min + (long long)b * step);
+    hi.n_reach.assign(h, 0);
+    for (int i = 0; i < h; ++i)
+        for (int b = hi.lo[i]; b < hi.lo[i] + w; ++b) hi.n_reach[i] += hi.reach[b];
+    for (int i = 0; i < h; ++i)
+        if (hi.n_reach[i] == 0) { why = "a window holds no realisable energy"; return REWL_EINVAL; }
+    int kf = 0;
+    while (std::ldexp(1.0, -kf) > d.ln_f_final) ++kf;
+    InstDev &I = hi.dev;
+    memset(&I, 0, sizeof I);
+    I.model = d.model;
+    I.L = d.L;
+    I.q = q;
+    I.N = (int)N;
+    I.wpr = d.model == REWL_ISING ? (d.L + 31) / 32 : 0;
+    I.lat_words = d.model == REWL_ISING ? d.L * I.wpr : (int)((N + 3) / 4);
+    I.magic_L = (uint32_t)((0x100000000ull + (ull)d.L - 1) / (ull)d.L);
+    I.step = step;
+    I.e_min = d.e_min;
+    I.B = B;
+    I.h = h;
+    I.m = d.walkers_per_window;
+    I.w = w;
+    I.stage_final = kf;
+    I.key0 = (uint32_t)d.seed;
+    I.key1 = (uint32_t)(d.seed >> 32) ^ d.instance_id;
+    I.p_flat = d.flatness;
+    return REWL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// creation
+// ---------------------------------------------------------------------------
+template <class T>
+static cudaError_t dalloc(T **p, size_t n)
+{
+    return cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T));
+}
+
+extern "C" void rewl_destroy(rewl_ctx *ctx);
+static rewl_status plan(rewl_ctx *ctx);
+
+extern "C" rewl_status rewl_create_batch(rewl_ctx **out, const rewl_instance *inst, int n_inst, void *cuda_stream)
+{
+    if (!out || !inst || n_inst < 1) return fail(nullptr, REWL_EINVAL, "rewl_create_batch: null argument or n_inst < 1");
+    *out = nullptr;
+    rewl_ctx *ctx = new rewl_ctx();
+    ctx->inst.resize(n_inst);
+    for (int k = 0; k < n_inst; ++k) {
+        std::string why;
+        rewl_status s = build_instance(inst[k], ctx->inst[k], why);
+        if (s != REWL_OK) {
+            delete ctx;
+            return fail(nullptr, s, "instance " + std::to_string(k) + ": " + why);
+        }
+    }
+    // offsets
+    long long lng = 0, lat = 0, rch = 0;
+    int win = 0, slot = 0;
+    std::vector<int32_t> lo_all, nreach_all, slot_inst;
+    std::vector<uint8_t> reach_all;
+    std::vector<ExTask> ex0, ex1;
+    for (int k = 0; k < n_inst; ++k) {
+        HostInst &h = ctx->inst[k];
+        InstDev &I = h.dev;
+        I.win0 = win;
+        I.slot0 = slot;
+        I.lng_off = lng;
+        I.lat_off = lat;
+        I.reach_off = (int)rch;
+        const int nw = I.h * I.m;
+        win += I.h;
+        slot += nw;
+        lng += (long long)nw * I.w;
+        lat += (long long)nw * I.lat_words;
+        rch += I.B;
+        for (int i = 0; i < I.h; ++i) {
+            lo_all.push_back(h.lo[i]);
+            nreach_all.push_back(h.n_reach[i]);
+        }
+        reach_all.insert(reach_all.end(), h.reach.begin(), h.reach.end());
+        for (int s = 0; s < nw; ++s) slot_inst.push_back(k);
+        for (int p = 0; p < 2; ++p)
+            for (int i = p; i + 1 < I.h; i += 2)
+                for (int j = 0; j < I.m; ++j) (p ? ex1 : ex0).push_back(ExTask{k, i, j, 0});
+    }
+    ctx->n_win = win;
+    ctx->n_slots = slot;
+    ctx->n_lng = lng;
+    ctx->n_lat = lat;
+    ctx->n_reach_bytes = rch;
+    ctx->n_ex0 = (int)ex0.size();
+    ctx->n_ex1 = (int)ex1.size();
+    if (cuda_stream) {
+        ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+        ctx->own_stream = true;
+    }
+    *out = ctx;  // from here on errors leave a context the caller destroys
+    std::vector<InstDev> idev;
+    for (auto &h : ctx->inst) idev.push_back(h.dev);
+    CK(dalloc(&ctx->d_inst, n_inst));
+    CK(dalloc(&ctx->d_lo, win));
+    CK(dalloc(&ctx->d_nreach, win));
+    CK(dalloc(&ctx->d_stage, win));
+    CK(dalloc(&ctx->d_conv, win));
+    CK(dalloc(&ctx->d_conv_sweep, win));
+    CK(dalloc(&ctx->d_ex_prop, win));
+    CK(dalloc(&ctx->d_ex_acc, win));
+    CK(dalloc(&ctx->d_cfg, slot));
+    CK(dalloc(&ctx->d_E, slot));
+    CK(dalloc(&ctx->d_bin, slot));
+    CK(dalloc(&ctx->d_replica, slot));
+    CK(dalloc(&ctx->d_slot_inst, slot));
+    CK(dalloc(&ctx->d_draw, slot));
+    CK(dalloc(&ctx->d_nacc, slot));
+    CK(dalloc(&ctx->d_latch, slot));
+    CK(dalloc(&ctx->d_lng, lng));
+    CK(dalloc(&ctx->d_H, lng));
+    CK(dalloc(&ctx->d_lat, lat));
+    CK(dalloc(&ctx->d_reach, rch));
+    CK(dalloc(&ctx->d_counters, 2));
+    CK(dalloc(&ctx->d_error, 1));
+    CK(dalloc(&ctx->d_ex0, ex0.size()));
+    CK(dalloc(&ctx->d_ex1, ex1.size()));
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemcpyAsync(ctx->d_inst, idev.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_lo, lo_all.data(), 4 * win, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_nreach, nreach_all.data(), 4 * win, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_reach, reach_all.data(), rch, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_slot_inst, slot_inst.data(), 4 * slot, cudaMemcpyHostToDevice, s));
+    if (!ex0.empty()) CK(cudaMemcpyAsync(ctx->d_ex0, ex0.data(), sizeof(ExTask) * ex0.size(), cudaMemcpyHostToDevice, s));
+    if (!ex1.empty()) CK(cudaMemcpyAsync(ctx->d_ex1, ex1.data(), sizeof(ExTask) * ex1.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctx->d_stage, 0, 4 * win, s));
+    CK(cudaMemsetAsync(ctx->d_conv, 0, win, s));
+    CK(cudaMemsetAsync(ctx->d_conv_sweep, 0xFF, 8 * win, s));
+    CK(cudaMemsetAsync(ctx->d_ex_prop, 0, 8 * win, s));
+    CK(cudaMemsetAsync(ctx->d_ex_acc, 0, 8 * win, s));
+    CK(cudaMemsetAsync(ctx->d_lng, 0, 8 * lng, s));
+    CK(cudaMemsetAsync(ctx->d_H, 0, 4 * lng, s));
+    CK(cudaMemsetAsync(ctx->d_counters, 0, 16, s));
+    CK(cudaMemsetAsync(ctx->d_error, 0, 4, s));
+    DevState &st = ctx->st;
+    st.inst = ctx->d_inst;
+    st.lo = ctx->d_lo;
+    st.n_reach = ctx->d_nreach;
+    st.stage = ctx->d_stage;
+    st.conv = ctx->d_conv;
+    st.conv_sweep = ctx->d_conv_sweep;
+    st.ex_prop = ctx->d_ex_prop;
+    st.ex_acc = ctx->d_ex_acc;
+    st.cfg = ctx->d_cfg;
+    st.E = ctx->d_E;
+    st.bin = ctx->d_bin;
+    st.draw = ctx->d_draw;
+    st.latch = ctx->d_latch;
+    st.n_acc = ctx->d_nacc;
+    st.replica = ctx->d_replica;
+    st.lng = ctx->d_lng;
+    st.H = ctx->d_H;
+    st.lat = ctx->d_lat;
+    st.reach = ctx->d_reach;
+    st.counters = ctx->d_counters;
+    st.error = ctx->d_error;
+    CK(cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming));
+    int e = launch_init(st, slot, ctx->d_slot_inst, s);
+    ctx->launches += 1;
+    if (e) return fail(ctx, REWL_ECUDA, std::string("init launch: ") + cudaGetErrorString((cudaError_t)e));
+    CK(cudaStreamSynchronize(s));
+    int herr = 0;
+    CK(cudaMemcpy(&herr, ctx->d_error, 4, cudaMemcpyDeviceToHost));
+    if (herr) return fail(ctx, REWL_EDEVICE, "init: a walker did not reach its window");
+    return REWL_OK;
+}
+
+extern "C" rewl_status rewl_create(rewl_ctx **out, rewl_model model, int L, int q, long e_min, long e_max,
+                                   int n_windows, double overlap, int walkers_per_window, double flatness,
+                                   double ln_f_final, unsigned long long seed, void *cuda_stream)
+{
+    rewl_instance d;
+    memset(&d, 0, sizeof d);
+    d.model = model;
+    d.L = L;
+    d.q = q;
+    d.n_windows = n_windows;
+    d.e_min = e_min;
+    d.e_max = e_max;
+    d.overlap = overlap;
+    d.walkers_per_window = walkers_per_window;
+    d.flatness = flatness;
+    d.ln_f_final = ln_f_final;
+    d.seed = seed;
+    d.instance_id = 0;
+    return rewl_create_batch(out, &d, 1, cuda_stream);
+}
+
+extern "C" void rewl_destroy(rewl_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    for (auto &c : ctx->classes) {
+        if (c.d_items) cudaFree(c.d_items);
+        if (c.stream) cudaStreamDestroy(c.stream);
+        if (c.done) cudaEventDestroy(c.done);
+    }
+    void *bufs[] = {ctx->d_inst, ctx->d_lo, ctx->d_nreach, ctx->d_stage, ctx->d_conv, ctx->d_conv_sweep,
+                    ctx->d_ex_prop, ctx->d_ex_acc, ctx->d_cfg, ctx->d_E, ctx->d_bin, ctx->d_replica,
+                    ctx->d_slot_inst, ctx->d_draw, ctx->d_nacc, ctx->d_latch, ctx->d_lng, ctx->d_H,
+                    ctx->d_lat, ctx->d_reach, ctx->d_counters, ctx->d_error, ctx->d_ex0, ctx->d_ex1};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (ctx->fork) cudaEventDestroy(ctx->fork);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+// ---------------------------------------------------------------------------
+// launch planning: one sweep launch per size class; the autotuner fills in
+// windows per block and lanes per walker (rewl_tune.cu)
+// ---------------------------------------------------------------------------
+
+void rewl::plan_class(rewl_ctx *ctx, int ci, int wpc, int lanes)
+{
+    SizeClass &c = ctx->classes[ci];
+    c.items.clear();
+    for (int k : c.insts) {
+        const InstDev &I = ctx->inst[k].dev;
+        for (int w0 = 0; w0 < I.h; w0 += wpc) c.items.push_back(WorkItem{k, w0, std::min(wpc, I.h - w0), 0});
+    }
+    const int nw = wpc * c.m;
+    c.sl.n_items = (int)c.items.size();
+    c.sl.lanes = lanes;
+    c.sl.threads = ((nw * lanes + 31) / 32) * 32;
+    c.sl.smem = sweep_smem_bytes(nw, wpc, c.w, c.lat_words);
+    c.sl.max_walkers = nw;
+    c.sl.max_w = c.w;
+    c.sl.max_lat_words = c.lat_words;
+    c.sl.max_win = wpc;
+    c.sl.model = c.model;
+}
+
+int rewl::class_count(const rewl_ctx *ctx) { return (int)ctx->classes.size(); }
+int rewl::class_walkers(const rewl_ctx *ctx, int ci)
+{
+    int n = 0;
+    for (int k : ctx->classes[ci].insts) n += ctx->inst[k].dev.h * ctx->inst[k].dev.m;
+    return n;
+}
+void rewl::class_shape(const rewl_ctx *ctx, int ci, int *model, int *N, int *w, int *m, int *lat_words)
+{
+    const SizeClass &c = ctx->classes[ci];
+    *model = c.model;
+    *N = c.N;
+    *w = c.w;
+    *m = c.m;
+    *lat_words = c.lat_words;
+}
+int rewl::total_walkers(const rewl_ctx *ctx) { return ctx->n_slots; }
+int rewl::forced_lanes(const rewl_ctx *ctx) { return ctx->force_lanes; }
+int rewl::forced_wpc(const rewl_ctx *ctx) { return ctx->force_wpc; }
+
+static rewl_status plan(rewl_ctx *ctx)
+{
+    if (ctx->planned) return REWL_OK;
+    std::map<std::vector<int>, int> key2c;
+    for (int k = 0; k < (int)ctx->inst.size(); ++k) {
+        const InstDev &I = ctx->inst[k].dev;
+        std::vector<int> key = {I.model, I.L, I.q, I.w, I.m};
+        auto f = key2c.find(key);
+        if (f == key2c.end()) {
+            SizeClass c;
+            c.model = I.model;
+            c.L = I.L;
+            c.q = I.q;
+            c.w = I.w;
+            c.m = I.m;
+            c.N = I.N;
+            c.lat_words = I.lat_words;
+            ctx->classes.push_back(c);
+            f = key2c.emplace(key, (int)ctx->classes.size() - 1).first;
+        }
+        ctx->classes[f->second].insts.push_back(k);
+    }
+    if (autotune_plan(ctx)) return fail(ctx, REWL_EINVAL, "no launch configuration fits a window's walkers in shared memory");
+    for (auto &c : ctx->classes) {
+        if (c.sl.smem > 227 * 1024) return fail(ctx, REWL_EINVAL, "window state exceeds shared memory");
+        CK(dalloc(&c.d_items, c.items.size()));
+        CK(cudaMemcpy(c.d_items, c.items.data(), sizeof(WorkItem) * c.items.size(), cudaMemcpyHostToDevice));
+        c.sl.items = c.d_items;
+        CK(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
+        int e = prepare_sweep(c.model, c.sl.lanes, c.sl.smem);
+        if (e) return fail(ctx, REWL_ECUDA, std::string("sweep kernel attributes: ") + cudaGetErrorString((cudaError_t)e));
+    }
+    ctx->planned = true;
+    return REWL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// running
+// ---------------------------------------------------------------------------
+static rewl_status check_usable(rewl_ctx *ctx)
+{
+    if (!ctx) return REWL_EINVAL;
+    if (ctx->failed) return REWL_ESTATE;
+    return REWL_OK;
+}
+
+static rewl_status enqueue_sweeps(rewl_ctx *ctx, long n)
+{
+    cudaStream_t s = ctx->stream;
+    while (n > 0) {
+        const long chunk = std::min(n, ctx->max_sweeps_per_launch);
+        if (ctx->classes.size() == 1) {
+            int e = launch_sweeps(ctx->st, ctx->classes[0].sl, chunk, ctx->check_every, s);
+            if (e) return fail(ctx, REWL_ECUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)e));
+        } else {
+            CK(cudaEventRecord(ctx->fork, s));
+            for (auto &c : ctx->classes) {
+                CK(cudaStreamWaitEvent(c.stream, ctx->fork, 0));
+                int e = launch_sweeps(ctx->st, c.sl, chunk, ctx->check_every, c.stream);
+                if (e) return fail(ctx, REWL_ECUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)e));
+                CK(cudaEventRecord(c.done, c.stream));
+                CK(cudaStreamWaitEvent(s, c.done, 0));
+            }
+        }
+        int e = launch_bump(ctx->st, chunk, 0, s);
+        if (e) return fail(ctx, REWL_ECUDA, std::string("counter launch: ") + cudaGetErrorString((cudaError_t)e));
+        ctx->launches += (long)ctx->classes.size() + 1;
+        n -= chunk;
+    }
+    return REWL_OK;
+}
+
+static rewl_status enqueue_exchange(rewl_ctx *ctx)
+{
+    if (ctx->n_ex0 + ctx->n_ex1 > 0) {
+        int e = launch_exchange(ctx->st, ctx->d_ex0, ctx->n_ex0, ctx->d_ex1, ctx->n_ex1, ctx->stream);
+        if (e) return fail(ctx, REWL_ECUDA, std::string("exchange launch: ") + cudaGetErrorString((cudaError_t)e));
+        ctx->launches += 1;
+    }
+    int e = launch_bump(ctx->st, 0, 1, ctx->stream);
+    if (e) return fail(ctx, REWL_ECUDA, std::string("counter launch: ") + cudaGetErrorString((cudaError_t)e));
+    ctx->launches += 1;
+    return REWL_OK;
+}
+
+extern "C" rewl_status rewl_run(rewl_ctx *ctx, long n_sweeps)
+{
+    rewl_status s = check_usable(ctx);
+    if (s) return s;
+    if (n_sweeps < 0) return fail(ctx, REWL_EINVAL, "n_sweeps < 0");
+    if ((s = plan(ctx))) return s;
+    return enqueue_sweeps(ctx, n_sweeps);
+}
+
+extern "C" rewl_status rewl_exchange(rewl_ctx *ctx)
+{
+    rewl_status s = check_usable(ctx);
+    if (s) return s;
+    return enqueue_exchange(ctx);
+}
+
+extern "C" rewl_status rewl_run_cycles(rewl_ctx *ctx, long n_cycles, long sweeps_per_cycle)
+{
+    rewl_status s = check_usable(ctx);
+    if (s) return s;
+    if (n_cycles < 0 || sweeps_per_cycle < 1) return fail(ctx, REWL_EINVAL, "n_cycles < 0 or sweeps_per_cycle < 1");
+    if ((s = plan(ctx))) return s;
+    if (ctx->graph_sweeps != sweeps_per_cycle) {
+        if (ctx->graph) {
+            cudaGraphExecDestroy(ctx->graph);
+            ctx->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        const long before = ctx->launches;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        rewl_status a = enqueue_sweeps(ctx, sweeps_per_cycle);
+        rewl_status b = a ? a : enqueue_exchange(ctx);
+        cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+        if (b) return b;
+        if (ce != cudaSuccess) return fail(ctx, REWL_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        ctx->graph_launches = ctx->launches - before;
+        ctx->launches = before;
+        cudaError_t ie = cudaGraphInstantiate(&ctx->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return fail(ctx, REWL_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+        ctx->graph_sweeps = sweeps_per_cycle;
+    }
+    for (long c = 0; c < n_cycles; ++c) {
+        CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+        ctx->launches += ctx->graph_launches;
+    }
+    return REWL_OK;
+}
+
+static rewl_status sync_and_check(rewl_ctx *ctx)
+{
+    CK(cudaStreamSynchronize(ctx->stream));
+    int herr = 0;
+    CK(cudaMemcpy(&herr, ctx->d_error, 4, cudaMemcpyDeviceToHost));
+    if (herr & kErrRange) return fail(ctx, REWL_EDEVICE, "ln g left the FP64-exact range |ln g| < 2^21");
+    if (herr) return fail(ctx, REWL_EDEVICE, "device error word " + std::to_string(herr));
+    return REWL_OK;
+}
+
+extern "C" rewl_status rewl_run_to_convergence(rewl_ctx *ctx, long exchange_interval, long max_sweeps,
+                                               long poll_cycles, int *converged)
+{
+    rewl_status s = check_usable(ctx);
+    if (s) return s;
+    if (exchange_interval < 1 || max_sweeps < 0 || poll_cycles < 1)
+        return fail(ctx, REWL_EINVAL, "exchange_interval, poll_cycles must be >= 1, max_sweeps >= 0");
+    if (converged) *converged = 0;
+    std::vector<uint8_t> conv(ctx->n_win);
+    long done = 0;
+    for (;;) {
+        if ((s = sync_and_check(ctx))) return s;
+        CK(cudaMemcpy(conv.data(), ctx->d_conv, ctx->n_win, cudaMemcpyDeviceToHost));
+        if (std::all_of(conv.begin(), conv.end(), [](uint8_t v) { return v != 0; })) {
+            if (converged) *converged = 1;
+            return REWL_OK;
+        }
+        if (done >= max_sweeps) return REWL_OK;
+        long cycles = std::min(poll_cycles, std::max(1L, (max_sweeps - done) / exchange_interval));
+        if ((s = rewl_run_cycles(ctx, cycles, exchange_interval))) return s;
+        done += cycles * exchange_interval;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// read-out
+// ---------------------------------------------------------------------------
+static rewl_status check_inst(rewl_ctx *ctx, int inst)
+{
+    if (!ctx) return REWL_EINVAL;
+    if (inst < 0 || inst >= (int)ctx->inst.size()) return fail(ctx, REWL_EINVAL, "instance index out of range");
+    if (ctx->failed) return REWL_ESTATE;
+    return REWL_OK;
+}
+
+extern "C" rewl_status rewl_geometry(rewl_ctx *ctx, int inst, int *hh, int *m, int *B, int *w, int *lo,
+                                     uint8_t *reach)
+{
+    if (!ctx || inst < 0 || inst >= (int)ctx->inst.size()) return REWL_EINVAL;
+    const HostInst &h = ctx->inst[inst];
+    if (hh) *hh = h.dev.h;
+    if (m) *m = h.dev.m;
+    if (B) *B = h.dev.B;
+    if (w) *w = h.dev.w;
+    if (lo) std::copy(h.lo.begin(), h.lo.end(), lo);
+    if (reach) std::copy(h.reach.begin(), h.reach.end(), reach);
+    return REWL_OK;
+}
+
+template <class T>
+static cudaError_t dget(std::vector<T> &v, const T *d, size_t n)
+{
+    v.resize(n);
+    if (n == 0) return cudaSuccess;
+    return cudaMemcpy(v.data(), d, n * sizeof(T), cudaMemcpyDeviceToHost);
+}
+
+extern "C" rewl_status rewl_get_state(rewl_ctx *ctx, int inst, int8_t *spins, int64_t *E, int32_t *bin,
+                                      double *ln_g, uint32_t *H, int32_t *stage, uint8_t *conv,
+                                      uint8_t *latch, int64_t *replica)
+{
+    rewl_status s = check_inst(ctx, inst);
+    if (s) return s;
+    if ((s = sync_and_check(ctx))) return s;
+    const InstDev &I = ctx->inst[inst].dev;
+    const int nw = I.h * I.m;
+    std::vector<int32_t> cfg, e, b, rep;
+    CK(dget(cfg, ctx->d_cfg + I.slot0, nw));
+    if (spins) {
+        std::vector<uint32_t> lat;
+        CK(dget(lat, ctx->d_lat + I.lat_off, (size_t)nw * I.lat_words));
+        for (int k = 0; k < nw; ++k) {
+            const uint32_t *l = lat.data() + (size_t)cfg[k] * I.lat_words;
+            for (int y = 0; y < I.L; ++y)
+                for (int x = 0; x < I.L; ++x) {
+                    int v;
+                    if (I.model == REWL_ISING) v = ((l[y * I.wpr + (x >> 5)] >> (x & 31)) & 1u) ? 1 : -1;
+                    else v = reinterpret_cast<const uint8_t *>(l)[y * I.L + x];
+                    spins[(size_t)k * I.N + y * I.L + x] = (int8_t)v;
+                }
+        }
+    }
+    if (E) {
+        CK(dget(e, ctx->d_E + I.slot0, nw));
+        for (int k = 0; k < nw; ++k) E[k] = e[k];
+    }
+    if (bin) CK(cudaMemcpy(bin, ctx->d_bin + I.slot0, 4 * nw, cudaMemcpyDeviceToHost));
+    if (ln_g) {
+        std::vector<long long> u;
+        CK(dget(u, ctx->d_lng + I.lng_off, (size_t)nw * I.w));
+        for (size_t i = 0; i < u.size(); ++i) ln_g[i] = std::ldexp((double)u[i], -32);
+    }
+    if (H) CK(cudaMemcpy(H, ctx->d_H + I.lng_off, 4 * (size_t)nw * I.w, cudaMemcpyDeviceToHost));
+    if (stage) CK(cudaMemcpy(stage, ctx->d_stage + I.win0, 4 * I.h, cudaMemcpyDeviceToHost));
+    if (conv) CK(cudaMemcpy(conv, ctx->d_conv + I.win0, I.h, cudaMemcpyDeviceToHost));
+    if (latch) CK(cudaMemcpy(latch, ctx->d_latch + I.slot0, nw, cudaMemcpyDeviceToHost));
+    if (replica) {
+        CK(dget(rep, ctx->d_replica + I.slot0, nw));
+        for (int k = 0; k < nw; ++k) replica[k] = rep[k];
+    }
+    return REWL_OK;
+}
+
+extern "C" rewl_status rewl_get_counters(rewl_ctx *ctx, int inst, uint64_t *ex_prop, uint64_t *ex_acc,
+                                         uint64_t *n_accepted, int64_t *conv_sweep)
+{
+    rewl_status s = check_inst(ctx, inst);
+    if (s) return s;
+    if ((s = sync_and_check(ctx))) return s;
+    const InstDev &I = ctx->inst[inst].dev;
+    if (ex_prop) CK(cudaMemcpy(ex_prop, ctx->d_ex_prop + I.win0, 8 * I.h, cudaMemcpyDeviceToHost));
+    if (ex_acc) CK(cudaMemcpy(ex_acc, ctx->d_ex_acc + I.win0, 8 * I.h, cudaMemcpyDeviceToHost));
+    if (n_accepted) CK(cudaMemcpy(n_accepted, ctx->d_nacc + I.slot0, 8 * (size_t)I.h * I.m, cudaMemcpyDeviceToHost));
+    if (conv_sweep) CK(cudaMemcpy(conv_sweep, ctx->d_conv_sweep + I.win0, 8 * I.h, cudaMemcpyDeviceToHost));
+    return REWL_OK;
+}
+
+extern "C" rewl_status rewl_status_query(rewl_ctx *ctx, int inst, int *all_converged, double *ln_f_per_window,
+                                         long *sweeps)
+{
+    rewl_status s = check_inst(ctx, inst);
+    if (s) return s;
+    if ((s = sync_and_check(ctx))) return s;
+    if (all_converged) {
+        std::vector<uint8_t> conv;
+        CK(dget(conv, ctx->d_conv, ctx->n_win));
+        *all_converged = std::all_of(conv.begin(), conv.end(), [](uint8_t v) { return v != 0; });
+    }
+    const InstDev &I = ctx->inst[inst].dev;
+    if (ln_f_per_window) {
+        std::vector<int32_t> st;
+        std::vector<uint8_t> cv;
+        CK(dget(st, ctx->d_stage + I.win0, I.h));
+        CK(dget(cv, ctx->d_conv + I.win0, I.h));
+        for (int i = 0; i < I.h; ++i) ln_f_per_window[i] = cv[i] ? 0.0 : std::ldexp(1.0, -st[i]);
+    }
+    if (sweeps) {
+        ull c[2];
+        CK(cudaMemcpy(c, ctx->d_counters, 16, cudaMemcpyDeviceToHost));
+        *sweeps = (long)c[0];
+    }
+    return REWL_OK;
+}
+
+// Sec. II B: join the pieces where their five-point inverse-temperature
+// estimates agree best, above the previous join; normalise at the first bin.
+static void join_pieces(const HostInst &h, const std::vector<double> &pieces, std::vector<double> &out)
+{
+    const InstDev &I = h.dev;
+    const int w = I.w, H = I.h, B = I.B, s = 1;
+    const double dE = I.step;
+    out.assign(B, NAN);
+    auto piece = [&](int i, int b) { return pieces[(size_t)i * w + (b - h.lo[i])]; };
+    auto beta = [&](int i, int b) {
+        return (piece(i, b - 2 * s) - 8.0 * piece(i, b - s) + 8.0 * piece(i, b + s) - piece(i, b + 2 * s)) /
+               (12.0 * s * dE);
+    };
+    double shift = 0.0;
+    int start = h.lo[0];
+    for (int i = 0; i + 1 < H; ++i) {
+        const int ov_lo = std::max(h.lo[i], h.lo[i + 1]);
+        const int ov_hi = std::min(h.lo[i] + w - 1, h.lo[i + 1] + w - 1);
+        int best = -1;
+        double best_d = 0.0;
+        for (int b = std::max(ov_lo, start + 1); b <= ov_hi; ++b) {
+            if (b - 2 * s < ov_lo || b + 2 * s > ov_hi) continue;
+            bool ok = true;
+            for (int d = -2; d <= 2; ++d) ok = ok && h.reach[b + d * s];
+            if (!ok) continue;
+            const double dd = std::fabs(beta(i, b) - beta(i + 1, b));
+            if (best < 0 || dd < best_d) {
+                best = b;
+                best_d = dd;
+            }
+        }
+        if (best < 0) {
+            best = std::max(ov_lo, start + 1);
+            while (best < ov_hi && !h.reach[best]) ++best;
+        }
+        for (int b = start; b < best; ++b) out[b] = piece(i, b) + shift;
+        shift = piece(i, best) + shift - piece(i + 1, best);
+        start = best;
+    }
+    for (int b = start; b < h.lo[H - 1] + w; ++b) out[b] = piece(H - 1, b) + shift;
+    int first = -1;
+    for (int b = 0; b < B; ++b) {
+        if (!h.reach[b]) out[b] = NAN;
+        else if (first < 0) first = b;
+    }
+    const double ln_min = std::log(I.model == REWL_ISING ? 2.0 : (double)I.q);
+    const double off = ln_min - out[first];
+    for (int b = 0; b < B; ++b) out[b] += off;
+}
+
+extern "C" rewl_status rewl_get_dos(rewl_ctx *ctx, int inst, double *ln_g, long cap, long *n_written,
+                                    long *e_of_bin, int per_window)
+{
+    rewl_status s = check_inst(ctx, inst);
+    if (s) return s;
+    if (!ln_g) return fail(ctx, REWL_EINVAL, "ln_g is NULL");
+    if ((s = sync_and_check(ctx))) return s;
+    const HostInst &h = ctx->inst[inst];
+    const InstDev &I = h.dev;
+    const long need = per_window ? (long)I.h * I.w : (long)I.B;
+    if (cap < need) return fail(ctx, REWL_EINVAL, "cap smaller than the result (" + std::to_string(need) + ")");
+    std::vector<long long> u;
+    CK(dget(u, ctx->d_lng + I.lng_off, (size_t)I.h * I.m * I.w));
+    std::vector<double> pieces((size_t)I.h * I.w);
+    for (int i = 0; i < I.h; ++i)
+        for (int b = 0; b < I.w; ++b) {
+            double acc = 0.0;
+            for (int j = 0; j < I.m; ++j) acc += std::ldexp((double)u[((size_t)i * I.m + j) * I.w + b], -32);
+            pieces[(size_t)i * I.w + b] = acc / I.m;
+        }
+    if (per_window) {
+        std::copy(pieces.begin(), pieces.end(), ln_g);
+        if (e_of_bin)
+            for (int i = 0; i < I.h; ++i)
+                for (int b = 0; b < I.w; ++b) e_of_bin[(size_t)i * I.w + b] = I.e_min + (long)(h.lo[i] + b) * I.step;
+    } else {
+        std::vector<double> out;
+        join_pieces(h, pieces, out);
+        std::copy(out.begin(), out.end(), ln_g);
+        if (e_of_bin)
+            for (int b = 0; b < I.B; ++b) e_of_bin[b] = I.e_min + (long)b * I.step;
+    }
+    if (n_written) *n_written = need;
+    return REWL_OK;
+}
+
+extern "C" rewl_status rewl_set_initial_lng(rewl_ctx *ctx, int inst, const double *ln_g0, double ln_f_start)
+{
+    rewl_status s = check_inst(ctx, inst);
+    if (s) return s;
+    if (!ln_g0) return fail(ctx, REWL_EINVAL, "ln_g0 is NULL");
+    int k0 = -1;
+    if (ln_f_start != 0.0) {
+        int e = 0;
+        const double mant = std::frexp(ln_f_start, &e);
+        if (mant != 0.5 || e > 1 || e < -31) return fail(ctx, REWL_EINVAL, "ln_f_start must be 0 or 2^-k, 0 <= k <= 32");
+        k0 = 1 - e;
+    }
+    if ((s = sync_and_check(ctx))) return s;
+    const HostInst &h = ctx->inst[inst];
+    const InstDev &I = h.dev;
+    std::vector<long long> u((size_t)I.h * I.m * I.w);
+    for (int i = 0; i < I.h; ++i)
+        for (int b = 0; b < I.w; ++b) {
+            double v = ln_g0[h.lo[i] + b];
+            if (!std::isfinite(v)) v = 0.0;
+            const double units = std::nearbyint(std::ldexp(v, 32));
+            if (!(std::fabs(units) < std::ldexp(1.0, 53))) return fail(ctx, REWL_EINVAL, "ln_g0 outside |ln g| < 2^21");
+            for (int j = 0; j < I.m; ++j) u[((size_t)i * I.m + j) * I.w + b] = (long long)units;
+        }
+    CK(cudaMemcpy(ctx->d_lng + I.lng_off, u.data(), 8 * u.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemset(ctx->d_H + I.lng_off, 0, 4 * u.size()));
+    CK(cudaMemset(ctx->d_latch + I.slot0, 0, (size_t)I.h * I.m));
+    std::vector<int32_t> st(I.h, k0 < 0 ? 0 : k0);
+    std::vector<uint8_t> cv(I.h, k0 < 0 ? 1 : 0);
+    CK(cudaMemcpy(ctx->d_stage + I.win0, st.data(), 4 * I.h, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_conv + I.win0, cv.data(), I.h, cudaMemcpyHostToDevice));
+    return REWL_OK;
+}
+
+extern "C" rewl_status rewl_set_option(rewl_ctx *ctx, int option, long value)
+{
+    if (!ctx) return REWL_EINVAL;
+    switch (option) {
+        case REWL_OPT_CHECK_EVERY:
+            if (value < 1) return fail(ctx, REWL_EINVAL, "check_every must be >= 1");
+            ctx->check_every = value;
+            break;
+        case REWL_OPT_LANES_PER_WALKER:
+            if (!(value == 0 || value == 1 || value == 2 || value == 4 || value == 8))
+                return fail(ctx, REWL_EINVAL, "lanes per walker must be 0, 1, 2, 4 or 8");
+            if (ctx->planned) return fail(ctx, REWL_ESTATE, "launch plan already fixed");
+            ctx->force_lanes = (int)value;
+            break;
+        case REWL_OPT_WINDOWS_PER_CTA:
+            if (value < 0) return fail(ctx, REWL_EINVAL, "windows per block must be >= 0");
+            if (ctx->planned) return fail(ctx, REWL_ESTATE, "launch plan already fixed");
+            ctx->force_wpc = (int)value;
+            break;
+        case REWL_OPT_MAX_SWEEPS_PER_LAUNCH:
+            if (value < 1) return fail(ctx, REWL_EINVAL, "max sweeps per launch must be >= 1");
+            ctx->max_sweeps_per_launch = value;
+            break;
+        default:
+            return fail(ctx, REWL_EINVAL, "unknown option");
+    }
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+        ctx->graph_sweeps = -1;
+    }
+    return REWL_OK;
+}
+
+extern "C" long rewl_launch_count(const rewl_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" const char *rewl_last_error(const rewl_ctx *ctx)
+{
+    if (!ctx) return g_create_error.c_str();
+    return ctx->err.c_str();
+}
+
+// ---------------------------------------------------------------------------
+// checkpoint
+// ---------------------------------------------------------------------------
+static const char kMagic[8] = {'R', 'E', 'W', 'L', 'C', 'K', 'P', '1'};
+
+template <class T>
+static bool wr(FILE *f, const std::vector<T> &v)
+{
+    const uint64_t n = v.size();
+    return fwrite(&n, 8, 1, f) == 1 && (n == 0 || fwrite(v.data(), sizeof(T), n, f) == n);
+}
+template <class T>
+static bool rd(FILE *f, std::vector<T> &v)
+{
+    uint64_t n = 0;
+    if (fread(&n, 8, 1, f) != 1) return false;
+    v.resize(n);
+    return n == 0 || fread(v.data(), sizeof(T), n, f) == n;
+}
+
+#define STATE_ARRAYS(X)                               \
+    X(int32_t, d_stage, ctx->n_win)                   \
+    X(uint8_t, d_conv, ctx->n_win)                    \
+    X(int64_t, d_conv_sweep, ctx->n_win)              \
+    X(ull, d_ex_prop, ctx->n_win)                     \
+    X(ull, d_ex_acc, ctx->n_win)                      \
+    X(int32_t, d_cfg, ctx->n_slots)                   \
+    X(int32_t, d_E, ctx->n_slots)                     \
+    X(int32_t, d_bin, ctx->n_slots)                   \
+    X(int32_t, d_replica, ctx->n_slots)               \
+    X(ull, d_draw, ctx->n_slots)                      \
+    X(ull, d_nacc, ctx->n_slots)                      \
+    X(uint8_t, d_latch, ctx->n_slots)                 \
+    X(long long, d_lng, (size_t)ctx->n_lng)           \
+    X(uint32_t, d_H, (size_t)ctx->n_lng)              \
+    X(uint32_t, d_lat, (size_t)ctx->n_lat)            \
+    X(ull, d_counters, 2)
+
+extern "C" rewl_status rewl_save(rewl_ctx *ctx, const char *path)
+{
+    rewl_status s = check_usable(ctx);
+    if (s) return s;
+    if (!path) return fail(ctx, REWL_EINVAL, "path is NULL");
+    if ((s = sync_and_check(ctx))) return s;
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(ctx, REWL_EINVAL, std::string("cannot open ") + path);
+    bool ok = fwrite(kMagic, 8, 1, f) == 1;
+    std::vector<rewl_instance> desc;
+    for (auto &h : ctx->inst) desc.push_back(h.desc);
+    ok = ok && wr(f, desc);
+    std::vector<long> opts = {ctx->check_every};
+    ok = ok && wr(f, opts);
+#define SAVE_ONE(T, field, n)                                     \
+    if (ok) {                                                     \
+        std::vector<T> v;                                         \
+        if (dget(v, ctx->field, n) != cudaSuccess) ok = false;    \
+        ok = ok && wr(f, v);                                      \
+    }
+    STATE_ARRAYS(SAVE_ONE)
+#undef SAVE_ONE
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) return fail(ctx, REWL_EINVAL, std::string("writing ") + path + " failed");
+    return REWL_OK;
+}
+
+extern "C" rewl_status rewl_load(rewl_ctx **out, const char *path, void *cuda_stream)
+{
+    if (!out || !path) return fail(nullptr, REWL_EINVAL, "rewl_load: null argument");
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(nullptr, REWL_EINVAL, std::string("cannot open ") + path);
+    char mg[8];
+    std::vector<rewl_instance> desc;
+    std::vector<long> opts;
+    bool ok = fread(mg, 8, 1, f) == 1 && memcmp(mg, kMagic, 8) == 0 && rd(f, desc) && rd(f, opts) && !desc.empty();
+    if (!ok) {
+        fclose(f);
+        return fail(nullptr, REWL_EINVAL, std::string(path) + " is not a REWL checkpoint");
+    }
+    rewl_status s = rewl_create_batch(out, desc.data(), (int)desc.size(), cuda_stream);
+    if (s) {
+        fclose(f);
+        return s;
+    }
+    rewl_ctx *ctx = *out;
+    ctx->check_every = opts.empty() ? 1 : opts[0];
+#define LOAD_ONE(T, field, n)                                                                           \
+    if (ok) {                                                                                           \
+        std::vector<T> v;                                                                               \
+        ok = rd(f, v) && v.size() == (size_t)(n);                                                      \
+        if (ok && cudaMemcpy(ctx->field, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess) \
+            ok = false;                                                                                 \
+    }
+    STATE_ARRAYS(LOAD_ONE)
+#undef LOAD_ONE
+    fclose(f);
+    if (!ok) return fail(ctx, REWL_EINVAL, std::string(path) + ": truncated or mismatched checkpoint");
+    return REWL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// primitive checks
+// ---------------------------------------------------------------------------
+extern "C" rewl_status rewl_debug_lam(const uint32_t *k_dev, int64_t *out_dev, long n)
+{
+    rewl_ctx *ctx = nullptr;
+    int e = launch_debug_lam(k_dev, out_dev, n, nullptr);
+    if (e) return fail(nullptr, REWL_ECUDA, cudaGetErrorString((cudaError_t)e));
+    CK(cudaDeviceSynchronize());
+    return REWL_OK;
+}
+
+extern "C" rewl_status rewl_debug_philox(uint32_t key0, uint32_t key1, const uint32_t *ctr_dev, uint32_t *out_dev,
+                                         long n)
+{
+    rewl_ctx *ctx = nullptr;
+    int e = launch_debug_philox(key0, key1, ctr_dev, out_dev, n, nullptr);
+    if (e) return fail(nullptr, REWL_ECUDA, cudaGetErrorString((cudaError_t)e));
+    CK(cudaDeviceSynchronize());
+    return REWL_OK;
+}

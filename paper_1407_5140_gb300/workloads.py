@@ -1,0 +1,64 @@
+"""Seeded workload descriptions shared by the tests, the benchmark and the oracle
+side of the parity checks.  Holds sizes, seeds and instance lists only -- none of
+the method's arithmetic.
+
+Each workload is a list of instance dicts with the fields of ``rewl_instance``
+(model 0 = Ising, 1 = Potts).
+"""
+import numpy as np
+
+ISING, POTTS = 0, 1
+
+
+def _inst(model, L, q, h, m, seed, instance_id=0, overlap=0.75, flatness=0.8, ln_f_final=2.0 ** -20):
+    N = L * L
+    return dict(model=model, L=L, q=q, e_min=-2 * N, e_max=(2 * N if model == ISING else 0), n_windows=h,
+                overlap=overlap, walkers_per_window=m, flatness=flatness, ln_f_final=ln_f_final, seed=seed,
+                instance_id=instance_id)
+
+
+def config0():
+    """2D Ising L=8, E in [-128, 128], 4 windows at 75 % overlap, 1 walker per
+    window, exchange every 1000 sweeps, Philox seed 0."""
+    return [_inst(ISING, 8, 2, 4, 1, 0)]
+
+
+def config1(sizes=(32, 64), seeds=32):
+    """Batched 2D Ising: L = 32 and 64, 16 windows at 75 %, 4 walkers per window,
+    32 independent seeds (0..31) per size, exchange every 10^4 sweeps."""
+    return [_inst(ISING, L, 2, 16, 4, s) for L in sizes for s in range(seeds)]
+
+
+def config2(seeds=1):
+    """2D q=10 Potts, L = 32, E in [-2048, 0], 32 windows at 75 %, 8 walkers per
+    window."""
+    return [_inst(POTTS, 32, 10, 32, 8, s) for s in range(seeds)]
+
+
+def config3(seed=3):
+    """Uneven batch: 64 Ising instances with L drawn from {16, 24, 32, 48, 64}
+    and 32 q=10 Potts instances with L from {16, 24, 32}; windows scale with the
+    energy range (h = clamp(round(N/128), 4, 32)) at 75 %; m = 8 (L <= 24), 4
+    (L = 32), 2 (L >= 48)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(64):
+        L = int(rng.choice([16, 24, 32, 48, 64]))
+        out.append(_inst(ISING, L, 2, _h(L), _m(L), 1000 + k))
+    for k in range(32):
+        L = int(rng.choice([16, 24, 32]))
+        out.append(_inst(POTTS, L, 10, _h(L), _m(L), 2000 + k))
+    return out
+
+
+def _h(L):
+    return int(min(32, max(4, round(L * L / 128))))
+
+
+def _m(L):
+    return 8 if L <= 24 else (4 if L == 32 else 2)
+
+
+def attempts_per_sweep(instances):
+    """Single-spin trials in one sweep of every walker of the batch."""
+    return sum(d["n_windows"] * d["walkers_per_window"] * d["L"] * d["L"] for d in instances)

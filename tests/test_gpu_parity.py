@@ -1,0 +1,230 @@
+"""GPU path vs CPU oracle, element by element, through the C ABI.
+
+Integer work (lattices, energies, bins, histograms, exchange decisions,
+counters) must be bit-exact; ln g is compared exactly too, because every value
+it takes is a multiple of 2^-32 held exactly on both sides.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import concat as cc
+from paper_1407_5140_gb300 import workloads as W
+
+from _pairs import assert_same_state, make_gpu, make_oracle, step_both
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+# ---------------------------------------------------------------------------
+# primitives
+# ---------------------------------------------------------------------------
+def test_lam_threshold_bit_exact_all_k():
+    torch = _torch()
+    from paper_1407_5140_gb300 import rewl as R
+    n = 1 << 24
+    k = torch.arange(n, dtype=torch.int64, device="cuda").to(torch.int32)
+    out = torch.empty(n, dtype=torch.int64, device="cuda")
+    R.debug_lam(k.data_ptr(), out.data_ptr(), n)
+    expect = O.lam_fix(np.arange(n, dtype=np.uint32))
+    got = out.cpu().numpy()
+    bad = np.nonzero(got != expect)[0]
+    assert bad.size == 0, f"{bad.size} thresholds differ, first k={bad[:5]}"
+
+
+def test_philox_bit_exact():
+    torch = _torch()
+    from paper_1407_5140_gb300 import rewl as R
+    rng = np.random.default_rng(7)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    for key in [(0, 0), (123, 456), (0xFFFFFFFF, 0x9E3779B9)]:
+        c = torch.from_numpy(ctr.view(np.int32)).cuda()
+        out = torch.empty_like(c)
+        R.debug_philox(key[0], key[1], c.data_ptr(), out.data_ptr(), ctr.shape[0])
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), O.philox(key, ctr))
+
+
+# ---------------------------------------------------------------------------
+# trajectories
+# ---------------------------------------------------------------------------
+def _ising(L, h, m, seed=0, **kw):
+    d = W._inst(W.ISING, L, 2, h, m, seed)
+    d.update(kw)
+    return d
+
+
+def _potts(L, q, h, m, seed=0, **kw):
+    d = W._inst(W.POTTS, L, q, h, m, seed)
+    d.update(kw)
+    return d
+
+
+CASES = [
+    ("ising_L8_h4_m1", _ising(8, 4, 1), 40, 3),
+    ("ising_L4_h1_m1", _ising(4, 1, 1, seed=9), 200, 2),
+    ("ising_L6_h2_m3", _ising(6, 2, 3, seed=5), 100, 3),
+    ("ising_L24_h6_m2", _ising(24, 6, 2, seed=2), 10, 2),
+    ("ising_L32_h16_m4", _ising(32, 16, 4, seed=1), 6, 2),
+    ("ising_L48_h8_m2", _ising(48, 8, 2, seed=4), 3, 2),
+    ("potts_q10_L32_h32_m8", _potts(32, 10, 32, 8, seed=0), 3, 2),
+    ("potts_q3_L4_h2_m2", _potts(4, 3, 2, 2, seed=6), 200, 3),
+    ("potts_q2_L8_h3_m2", _potts(8, 2, 3, 2, seed=8), 50, 2),
+    ("ising_L8_partial_range", _ising(8, 3, 2, seed=3, e_min=-120, e_max=40), 40, 3),
+]
+
+
+@pytest.mark.parametrize("name,d,sweeps,cycles", CASES, ids=[c[0] for c in CASES])
+def test_trajectory_matches_oracle(name, d, sweeps, cycles):
+    gpu = make_gpu([d])
+    orc = make_oracle(d)
+    orc.init()
+    assert_same_state(gpu, 0, orc, f"{name} after init")
+    for c in range(cycles):
+        step_both(gpu, [orc], sweeps)
+        assert_same_state(gpu, 0, orc, f"{name} cycle {c}")
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+@pytest.mark.parametrize("wpc", [1, 3])
+def test_launch_shape_does_not_change_results(lanes, wpc):
+    d = _ising(16, 6, 2, seed=11)
+    gpu = make_gpu([d], lanes_per_walker=lanes, windows_per_cta=wpc)
+    orc = make_oracle(d)
+    orc.init()
+    for c in range(3):
+        step_both(gpu, [orc], 25)
+    assert_same_state(gpu, 0, orc, f"lanes={lanes} wpc={wpc}")
+
+
+def test_potts_lanes_and_check_every():
+    d = _potts(16, 10, 8, 4, seed=12)
+    for lanes, ce in [(1, 1), (4, 3), (8, 1)]:
+        gpu = make_gpu([d], lanes_per_walker=lanes, check_every=ce)
+        orc = make_oracle(d)
+        orc.set_check_every(ce)
+        orc.init()
+        for c in range(3):
+            step_both(gpu, [orc], 20)
+        assert_same_state(gpu, 0, orc, f"lanes={lanes} check_every={ce}")
+
+
+def test_batch_of_mixed_instances_matches_each_oracle():
+    ds = [_ising(8, 4, 1, seed=0), _potts(8, 10, 4, 2, seed=1), _ising(16, 5, 3, seed=2),
+          _ising(8, 4, 1, seed=0, instance_id=7), _potts(12, 4, 3, 2, seed=3)]
+    gpu = make_gpu(ds)
+    orcs = [make_oracle(d) for d in ds]
+    for o in orcs:
+        o.init()
+    for c in range(3):
+        step_both(gpu, orcs, 30)
+        for k, o in enumerate(orcs):
+            assert_same_state(gpu, k, o, f"instance {k} cycle {c}")
+
+
+def test_full_convergence_config0_bit_exact_and_accurate():
+    d = W.config0()[0]
+    gpu = make_gpu([d])
+    orc = make_oracle(d)
+    orc.init()
+    for c in range(200):
+        step_both(gpu, [orc], 1000)
+        if orc.all_converged():
+            break
+    assert orc.all_converged()
+    assert gpu.status(0)["all_converged"]
+    assert_same_state(gpu, 0, orc, "config0 converged")
+    ex = _golden_lng(8, 65)
+    lg, _ = gpu.get_dos(0)
+    eps = cc.mean_relative_error(lg, ex)
+    olg, _ = cc.concatenate(orc.pieces(), orc.lo, orc.w, orc.reach, 4.0, math.log(2))
+    assert np.allclose(lg, olg, equal_nan=True, atol=1e-9)       # host-side join agrees
+    assert eps < 0.03, eps
+
+
+def test_graph_cycles_equal_stepwise_calls():
+    d = _ising(16, 4, 2, seed=21)
+    a = make_gpu([d])
+    b = make_gpu([d])
+    a.run_cycles(5, 30)
+    for _ in range(5):
+        b.run(30)
+        b.exchange()
+    sa, sb = a.state(0, 256), b.state(0, 256)
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+
+
+def test_checkpoint_resume_is_bit_exact(tmp_path):
+    from paper_1407_5140_gb300 import rewl as R
+    d = _potts(8, 10, 4, 2, seed=5)
+    a = make_gpu([d])
+    a.run_cycles(3, 40)
+    p = str(tmp_path / "ck.bin")
+    a.save(p)
+    b = R.Rewl.load(p)
+    a.run_cycles(4, 40)
+    b.run_cycles(4, 40)
+    sa, sb = a.state(0, 64), b.state(0, 64)
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+
+
+def test_warm_start_and_frozen_sampling_match_oracle():
+    d = _ising(8, 4, 2, seed=13)
+    ex = _golden_lng(8, 65)
+    for lnf in (2.0 ** -4, 0.0):
+        gpu = make_gpu([d])
+        gpu.set_initial_lng(0, np.nan_to_num(ex), lnf)
+        orc = make_oracle(d)
+        orc.init()
+        orc.set_lng(np.nan_to_num(ex), 4 if lnf else -1)
+        for c in range(3):
+            step_both(gpu, [orc], 50)
+        assert_same_state(gpu, 0, orc, f"warm start ln f = {lnf}")
+
+
+def test_config1_launch_sampled_instances_match_oracle():
+    # the benchmark's workload and launch shape; three instances per size are
+    # re-run on the oracle and compared element by element
+    ds = W.config1()
+    gpu = make_gpu(ds)
+    gpu.run(4)
+    gpu.exchange()
+    gpu.run(2)
+    for k in (0, 17, 31, 32, 50, 63):
+        o = make_oracle(ds[k])
+        o.init()
+        o.run(4)
+        o.exchange()
+        o.run(2)
+        assert_same_state(gpu, k, o, f"config1 instance {k}")
+
+
+def test_invalid_arguments_fail_cleanly():
+    from paper_1407_5140_gb300 import rewl as R
+    for bad in [dict(L=7), dict(L=3), dict(n_windows=0), dict(overlap=1.0), dict(e_min=-130),
+                dict(e_min=-126), dict(ln_f_final=0.0)]:
+        d = _ising(8, 4, 1)
+        d.update(bad)
+        with pytest.raises(R.RewlError) as ei:
+            make_gpu([d])
+        assert ei.value.code == -1
+
+
+def _golden_lng(L, B):
+    rows = np.loadtxt(os.path.join(GOLDEN, f"ising_L{L}_exact_lng.txt"), usecols=(0, 1))
+    out = np.full(B, np.nan)
+    N = L * L
+    for E, lg in rows:
+        out[(int(E) + 2 * N) // 4] = lg
+    return out
