@@ -1,0 +1,319 @@
+"""Benchmark: Wang-Landau flip attempts per second of the replica-exchange
+Wang-Landau path on the batched 2D Ising workload (L = 32 and L = 64, 16
+windows x 4 walkers per window at 75 % overlap, 32 seeds per size, exchange
+every 10^4 sweeps) -- one step = 10^4 sweeps of every walker plus one exchange
+phase, replayed from the library's CUDA graph.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is device-timed (CUDA events on the library's
+stream, L2 flushed between steps); `e2e` is wall-clock through the public API
+with host descriptors in and ln g pieces out every step; `roofline` relates the
+sweep kernel's issue rate to the GPU's thread-instruction peak; `cpu_baseline`
+is the CPU oracle on the host cores on a bounded sample of the same workload.
+Under torchrun each rank runs its own batch (distinct seeds, weak scaling).
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SWEEPS_PER_STEP = 10_000
+# Algorithmic thread-instructions of one single-spin trial (derivation in
+# the design doc): Philox4x32-10 share, site and neighbour indices, the -ln u
+# threshold, neighbour reads and the energy change, the ln g lookup and
+# comparison, the accepted move, and the ln g / H updates.
+INSTR_PER_TRIAL = {0: 110, 1: 146}
+N_SM = 152
+MAX_SM_MHZ = 2070.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        idx = vis.split(",")[self.gpu] if vis and vis.split(",")[0].isdigit() else str(self.gpu)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", idx, f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), hw=f[5], hwt=f[6], swt=f[7], pcap=f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        reasons = set()
+        for r in rows:
+            for k, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                            ("pcap", "sw_power_cap")):
+                if r[k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _traffic_from_profile(kernel_src_sha):
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "sweep_kernel_ising_config1.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
+    t = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != kernel_src_sha:
+        return None
+    return float(t.group(1))
+
+
+def _kernel_sha():
+    h = hashlib.sha256()
+    for f in ("rewl_kernels.cu", "rewl_device.cuh", "rewl_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1407_5140_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def cpu_oracle_rate(ds, budget_s, threads):
+    """Oracle attempts/s on whole instances of the workload, sweeps in chunks until
+    the time budget is spent."""
+    import oracle as O
+    done = 0
+    t0 = time.perf_counter()
+    used = []
+    for d in ds:
+        o = O.Oracle(d["model"], d["L"], d["q"], d["e_min"], d["e_max"], d["n_windows"], d["overlap"],
+                     d["walkers_per_window"], d["flatness"], d["ln_f_final"], seed=d["seed"],
+                     instance=d["instance_id"], threads=threads)
+        o.init()
+        t_init = time.perf_counter()
+        chunk = 5
+        sweeps = 0
+        while time.perf_counter() - t0 < budget_s * (len(used) + 1) / len(ds):
+            o.run(chunk)
+            sweeps += chunk
+        t_run = time.perf_counter() - t_init
+        used.append((d, sweeps, t_run))
+        done += sweeps * d["n_windows"] * d["walkers_per_window"] * d["L"] ** 2
+    total_t = sum(u[2] for u in used)
+    desc = "; ".join(f"{d['walkers_per_window'] * d['n_windows']} walkers L={d['L']} x {s} sweeps"
+                     for d, s, _ in used)
+    return done / total_t, desc, total_t
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_1407_5140_gb300 import rewl as R
+    from paper_1407_5140_gb300 import workloads as W
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    ds = W.config1()
+    for d in ds:                       # weak scaling: each rank its own seeds
+        d["seed"] += 1000 * rank
+    attempts_per_step = W.attempts_per_sweep(ds) * SWEEPS_PER_STEP
+    stream = torch.cuda.current_stream()
+    ctx = R.Rewl([R.instance(**d) for d in ds], stream=stream)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        ctx.run_cycles(1, SWEEPS_PER_STEP)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches0 = ctx.launch_count()
+    times = []
+    with ClockSampler(dev) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.run_cycles(1, SWEEPS_PER_STEP)
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b) / 1000.0)
+        torch.cuda.synchronize()
+    launches = ctx.launch_count() - launches0
+    t_step = sum(times) / len(times)
+    if world > 1:
+        tt = torch.tensor([t_step], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = attempts_per_step * world / t_step
+    clocks = clk.summary()
+
+    # sweep-kernel launch duration alone (CUDA events on the library's stream)
+    ks = []
+    for _ in range(3):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.run(SWEEPS_PER_STEP)
+        b.record(stream)
+        b.synchronize()
+        ks.append(a.elapsed_time(b) / 1000.0)
+    k_time = sum(ks) / len(ks)
+    ctx.close()
+
+    # end to end through the public API: descriptors in (host), ln g out (host)
+    t0 = time.perf_counter()
+    e2e_ctx = R.Rewl([R.instance(**d) for d in ds], stream=stream)
+    d2h = 0
+    for _ in range(args.steps):
+        e2e_ctx.run_cycles(1, SWEEPS_PER_STEP)
+        for k in range(len(ds)):
+            p, _e = e2e_ctx.get_dos(k, per_window=True)
+            d2h += p.nbytes
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    e2e_ctx.close()
+    h2d = len(ds) * 88
+    e2e = {"value": attempts_per_step * args.steps / e2e_t * world, "unit": "attempts/s",
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+           "includes": "create (descriptors H2D, init kernel) + K steps + per-step ln g read-back"}
+
+    instr = INSTR_PER_TRIAL[0]
+    peak_instr = N_SM * 4 * 32 * MAX_SM_MHZ * 1e6
+    achieved = instr * attempts_per_step / k_time
+    sha = _kernel_sha()
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_instr / 1e12, "unit": "Tinstr/s",
+                "frac": achieved / peak_instr, "traffic": _traffic_from_profile(sha),
+                "peak_source": f"{N_SM} SMs x 4 schedulers x 32 lanes x {MAX_SM_MHZ:.0f} MHz (max SM clock)",
+                "instr_per_trial": instr, "kernel_time_s": k_time}
+    return dict(value=value, t_step=t_step, e2e=e2e, roofline=roofline, clocks=clocks, launches=launches,
+                attempts_per_step=attempts_per_step, ds=ds)
+
+
+def profile_case():
+    """The benchmark's batch and launch shape with short launches: two cycles
+    of 20 sweeps + exchange, for ncu (kernel durations of a few ms)."""
+    import torch
+    from paper_1407_5140_gb300 import rewl as R
+    from paper_1407_5140_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    ds = W.config1()
+    ctx = R.Rewl([R.instance(**d) for d in ds], stream=torch.cuda.current_stream())
+    for _ in range(2):
+        ctx.run(20)
+        ctx.exchange()
+    torch.cuda.synchronize()
+    st = ctx.status(0)
+    ctx.close()
+    print(json.dumps({"profile_case": "config1 batch, 2 x (20 sweeps + exchange)", "sweeps": st["sweeps"]}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--profile-case", action="store_true",
+                    help="only the workload's launch shape with 20 sweeps per launch (for ncu captures)")
+    args = ap.parse_args()
+    if args.profile_case:
+        profile_case()
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    threads = os.cpu_count() or 1
+    from paper_1407_5140_gb300 import workloads as W
+    workload = ("2D Ising REWL batch: L=32 and L=64, 16 windows x 4 walkers at 75% overlap, "
+                "32 seeds per size (4096 walkers), 10^4 sweeps + 1 exchange per step")
+    config = {"workload": workload, "instances": 64, "walkers": 4096, "sweeps_per_step": SWEEPS_PER_STEP,
+              "l2": "flushed between steps (256 MiB write)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle  # noqa: F401  (C oracle, built by build())
+        ds = W.config1()
+        sample = [ds[0], ds[32]]
+        rates = []
+        for _ in range(args.warmup + args.steps):
+            r, desc, t = cpu_oracle_rate(sample, args.cpu_budget / max(1, args.steps), threads)
+            rates.append(r)
+        v = statistics.mean(rates[args.warmup:])
+        print(json.dumps({"impl": "reference", "metric": "WL flip attempts/s", "value": v, "unit": "attempts/s",
+                          "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": W.attempts_per_sweep(ds) * SWEEPS_PER_STEP / v * 1e3,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": config,
+                          "cpu_baseline": {"value": v, "unit": "attempts/s", "cores": threads, "kind": "oracle",
+                                           "sample": "per step: " + desc},
+                          "e2e": {"value": v, "unit": "attempts/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    r = run_ours(args, rank, world)
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1:
+        ds = r["ds"]
+        v, desc, t = cpu_oracle_rate([ds[0], ds[32]], args.cpu_budget, threads)
+        cpu = {"value": v, "unit": "attempts/s", "cores": threads, "kind": "oracle",
+               "sample": desc + f" ({t:.1f} s of oracle time)"}
+    out = {"metric": "WL flip attempts/s", "value": r["value"], "unit": "attempts/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["t_step"] * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic", "config": config,
+           "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"], "clocks": r["clocks"],
+           "gpu_launches": r["launches"]}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
