@@ -158,7 +158,10 @@ def run_ours(args, rank, world):
     for d in ds:                       # weak scaling: each rank its own seeds
         d["seed"] += 1000 * rank
     attempts_per_step = W.attempts_per_sweep(ds) * SWEEPS_PER_STEP
-    stream = torch.cuda.current_stream()
+    # a stream of our own: torch's default stream has handle 0, which the
+    # library would replace by a stream it creates
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     ctx = R.Rewl([R.instance(**d) for d in ds], stream=stream)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
@@ -237,7 +240,9 @@ def profile_case():
     from paper_1407_5140_gb300 import workloads as W
     torch.cuda.set_device(0)
     ds = W.config1()
-    ctx = R.Rewl([R.instance(**d) for d in ds], stream=torch.cuda.current_stream())
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = R.Rewl([R.instance(**d) for d in ds], stream=stream)
     for _ in range(2):
         ctx.run(20)
         ctx.exchange()

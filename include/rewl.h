@@ -66,7 +66,7 @@ typedef struct rewl_instance {
     int32_t n_windows;          /* h >= 1                                       */
     int64_t e_min, e_max;       /* inclusive energy range, on the bin grid      */
     double overlap;             /* o in [0, 1)                                  */
-    int32_t walkers_per_window; /* m >= 1                                       */
+    int32_t walkers_per_window; /* m, 1..32                                     */
     int32_t reserved;
     double flatness;            /* p in (0, 1]: flat iff min H >= p <H>         */
     double ln_f_final;          /* run ends after the stage with ln f <= this   */
@@ -156,10 +156,12 @@ rewl_status rewl_get_counters(rewl_ctx *ctx, int inst, uint64_t *ex_prop, uint64
                               uint64_t *n_accepted, int64_t *conv_sweep);
 
 /* Options.  REWL_OPT_CHECK_EVERY: sweeps between flatness tests (>= 1).
- * REWL_OPT_LANES_PER_WALKER: force the autotuner's lanes-per-walker (0 = auto).
- * REWL_OPT_WINDOWS_PER_CTA: force windows per thread block (0 = auto).
- * REWL_OPT_MAX_SWEEPS_PER_LAUNCH: split long rewl_run calls (>= 1). */
-enum { REWL_OPT_CHECK_EVERY = 1, REWL_OPT_LANES_PER_WALKER = 2, REWL_OPT_WINDOWS_PER_CTA = 3,
+ * REWL_OPT_PRODUCER_WARPS: force the autotuner's producer warps per thread
+ * block (0 = auto, 1..4).  REWL_OPT_WINDOWS_PER_CTA: force windows per thread
+ * block (0 = auto; at most 32 walkers per block).
+ * REWL_OPT_MAX_SWEEPS_PER_LAUNCH: split long rewl_run calls (>= 1).
+ * Launch-shape options may only be set before the first run. */
+enum { REWL_OPT_CHECK_EVERY = 1, REWL_OPT_PRODUCER_WARPS = 2, REWL_OPT_WINDOWS_PER_CTA = 3,
        REWL_OPT_MAX_SWEEPS_PER_LAUNCH = 4 };
 rewl_status rewl_set_option(rewl_ctx *ctx, int option, long value);
 

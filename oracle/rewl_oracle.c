@@ -495,8 +495,11 @@ int oracle_run(rewl_oracle *o, long n_sweeps, int n_threads)
 #else
     (void)n_threads;
 #endif
+    /* walkers are independent within a sweep; small instances run serially
+     * (a team's barrier per sweep costs more than the sweep itself) */
+    const long work = (long)o->n_walkers * o->N;
     for (long sw = 0; sw < n_sweeps; ++sw) {
-        #pragma omp parallel for schedule(dynamic, 1)
+        #pragma omp parallel for schedule(dynamic, 1) if (work >= 65536 && o->n_walkers >= 4)
         for (int k = 0; k < o->n_walkers; ++k) walker_sweep(o, k);
         o->sweeps += 1;
         if (o->sweeps % o->check_every == 0)

@@ -66,7 +66,7 @@ struct rewl_ctx {
     cudaEvent_t fork = nullptr;
     long check_every = 1;
     long max_sweeps_per_launch = 1L << 30;
-    int force_lanes = 0, force_wpc = 0;
+    int force_producers = 0, force_wpc = 0;
     bool planned = false;
     cudaGraphExec_t graph = nullptr;
     long graph_sweeps = -1;
@@ -120,7 +120,7 @@ static rewl_status build_instance(const rewl_instance &d, HostInst &hi, std::str
     const int q = d.model == REWL_ISING ? 2 : d.q;
     if (d.model == REWL_POTTS && (q < 2 || q > 127)) { why = "q must be in 2..127"; return REWL_EINVAL; }
     if (d.n_windows < 1 || d.n_windows > 65535) { why = "n_windows must be in 1..65535"; return REWL_EINVAL; }
-    if (d.walkers_per_window < 1 || d.walkers_per_window > 1024) { why = "walkers_per_window must be in 1..1024"; return REWL_EINVAL; }
+    if (d.walkers_per_window < 1 || d.walkers_per_window > 32) { why = "walkers_per_window must be in 1..32"; return REWL_EINVAL; }
     if (!(d.overlap >= 0.0 && d.overlap < 1.0)) { why = "overlap must be in [0, 1)"; return REWL_EINVAL; }
     if (!(d.flatness > 0.0 && d.flatness <= 1.0)) { why = "flatness must be in (0, 1]"; return REWL_EINVAL; }
     if (!(d.ln_f_final >= std::ldexp(1.0, -32) && d.ln_f_final <= 1.0)) { why = "ln_f_final must be in [2^-32, 1]"; return REWL_EINVAL; }
@@ -369,7 +369,7 @@ extern "C" void rewl_destroy(rewl_ctx *ctx)
 // windows per block and lanes per walker (rewl_tune.cu)
 // ---------------------------------------------------------------------------
 
-void rewl::plan_class(rewl_ctx *ctx, int ci, int wpc, int lanes)
+void rewl::plan_class(rewl_ctx *ctx, int ci, int wpc, int producers)
 {
     SizeClass &c = ctx->classes[ci];
     c.items.clear();
@@ -379,8 +379,8 @@ void rewl::plan_class(rewl_ctx *ctx, int ci, int wpc, int lanes)
     }
     const int nw = wpc * c.m;
     c.sl.n_items = (int)c.items.size();
-    c.sl.lanes = lanes;
-    c.sl.threads = ((nw * lanes + 31) / 32) * 32;
+    c.sl.producers = producers;
+    c.sl.threads = 32 * (1 + producers);
     c.sl.smem = sweep_smem_bytes(nw, wpc, c.w, c.lat_words);
     c.sl.max_walkers = nw;
     c.sl.max_w = c.w;
@@ -406,7 +406,7 @@ void rewl::class_shape(const rewl_ctx *ctx, int ci, int *model, int *N, int *w, 
     *lat_words = c.lat_words;
 }
 int rewl::total_walkers(const rewl_ctx *ctx) { return ctx->n_slots; }
-int rewl::forced_lanes(const rewl_ctx *ctx) { return ctx->force_lanes; }
+int rewl::forced_producers(const rewl_ctx *ctx) { return ctx->force_producers; }
 int rewl::forced_wpc(const rewl_ctx *ctx) { return ctx->force_wpc; }
 
 static rewl_status plan(rewl_ctx *ctx)
@@ -432,6 +432,10 @@ static rewl_status plan(rewl_ctx *ctx)
         ctx->classes[f->second].insts.push_back(k);
     }
     if (autotune_plan(ctx)) return fail(ctx, REWL_EINVAL, "no launch configuration fits a window's walkers in shared memory");
+    // launch the classes with the largest blocks first: the block scheduler then
+    // packs the smaller blocks into the shared memory the large ones leave free
+    std::stable_sort(ctx->classes.begin(), ctx->classes.end(),
+                     [](const SizeClass &a, const SizeClass &b) { return a.sl.smem > b.sl.smem; });
     for (auto &c : ctx->classes) {
         if (c.sl.smem > 227 * 1024) return fail(ctx, REWL_EINVAL, "window state exceeds shared memory");
         CK(dalloc(&c.d_items, c.items.size()));
@@ -439,7 +443,15 @@ static rewl_status plan(rewl_ctx *ctx)
         c.sl.items = c.d_items;
         CK(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
-        int e = prepare_sweep(c.model, c.sl.lanes, c.sl.smem);
+    }
+    // one kernel per model serves every class of that model: allow the largest
+    // dynamic shared memory any of them needs
+    for (int model = 0; model < 2; ++model) {
+        int smem = 0;
+        for (auto &c : ctx->classes)
+            if (c.model == model) smem = std::max(smem, c.sl.smem);
+        if (!smem) continue;
+        int e = prepare_sweep(model, 0, smem);
         if (e) return fail(ctx, REWL_ECUDA, std::string("sweep kernel attributes: ") + cudaGetErrorString((cudaError_t)e));
     }
     ctx->planned = true;
@@ -826,11 +838,10 @@ extern "C" rewl_status rewl_set_option(rewl_ctx *ctx, int option, long value)
             if (value < 1) return fail(ctx, REWL_EINVAL, "check_every must be >= 1");
             ctx->check_every = value;
             break;
-        case REWL_OPT_LANES_PER_WALKER:
-            if (!(value == 0 || value == 1 || value == 2 || value == 4 || value == 8))
-                return fail(ctx, REWL_EINVAL, "lanes per walker must be 0, 1, 2, 4 or 8");
+        case REWL_OPT_PRODUCER_WARPS:
+            if (value < 0 || value > 4) return fail(ctx, REWL_EINVAL, "producer warps must be in 0..4");
             if (ctx->planned) return fail(ctx, REWL_ESTATE, "launch plan already fixed");
-            ctx->force_lanes = (int)value;
+            ctx->force_producers = (int)value;
             break;
         case REWL_OPT_WINDOWS_PER_CTA:
             if (value < 0) return fail(ctx, REWL_EINVAL, "windows per block must be >= 0");

@@ -88,8 +88,8 @@ struct DevState {
 struct SweepLaunch {
     const WorkItem *items;  // device array
     int n_items;
-    int threads;            // per block
-    int lanes;              // lanes per walker (1, 2, 4, 8)
+    int threads;            // per block: 32 * (1 consumer warp + producers)
+    int producers;          // producer warps per block (1..4)
     int smem;               // dynamic shared memory bytes
     int max_walkers;        // walkers per block (n_win * m) upper bound
     int max_w;              // window width upper bound
@@ -105,7 +105,7 @@ int launch_exchange(const DevState &st, const ExTask *tasks0, int n0, const ExTa
                     void *stream);
 int launch_bump(const DevState &st, long sweeps, long exchanges, void *stream);
 int sweep_smem_bytes(int n_walkers, int n_win, int w, int lat_words);
-int prepare_sweep(int model, int lanes, int smem);
+int prepare_sweep(int model, int producers, int smem);
 int launch_debug_lam(const uint32_t *k, int64_t *out, long n, void *stream);
 int launch_debug_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr, uint32_t *out, long n,
                         void *stream);
@@ -116,11 +116,11 @@ int launch_debug_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr, uint32_t 
 struct rewl_ctx;
 namespace rewl {
 int autotune_plan(rewl_ctx *ctx);
-void plan_class(rewl_ctx *ctx, int c, int wpc, int lanes);
+void plan_class(rewl_ctx *ctx, int c, int wpc, int producers);
 int class_count(const rewl_ctx *ctx);
 int class_walkers(const rewl_ctx *ctx, int c);
 void class_shape(const rewl_ctx *ctx, int c, int *model, int *N, int *w, int *m, int *lat_words);
 int total_walkers(const rewl_ctx *ctx);
-int forced_lanes(const rewl_ctx *ctx);
+int forced_producers(const rewl_ctx *ctx);
 int forced_wpc(const rewl_ctx *ctx);
 }  // namespace rewl

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "rewl_device.cuh"
 #include "rewl_internal.h"
 
@@ -111,15 +113,22 @@ __global__ void init_kernel(DevState st, int n_slots, const int32_t *slot_inst)
 // ---------------------------------------------------------------------------
 // sweeps
 // ---------------------------------------------------------------------------
+// Trials per producer round and walker (a round is one slot of the ring).
+static constexpr int kR = 32;
+// Guard bins on each side of a walker's ln g array: the consumer reads ln g of
+// the bins b-4..b+4 speculatively before it knows the energy change.
+static constexpr int kGuard = 4;
+
 int sweep_smem_bytes(int n_walkers, int n_win, int w, int lat_words)
 {
     long long b = 0;
-    b += (long long)n_walkers * w * 8;             // ln g
-    b += (long long)n_walkers * w * 4;             // H
-    b += (long long)n_walkers * lat_words * 4;     // lattices
-    b += ((long long)n_win * w + 15) / 16 * 16;    // reach
-    b += (long long)n_win * 16;                    // window state
-    b += ((long long)n_walkers + 15) / 16 * 16;    // latch
+    b += 2LL * n_walkers * kR * 48;                     // trial ring, 2 slots (48-byte records)
+    b += (long long)n_walkers * (w + 2 * kGuard) * 8;   // ln g with guards
+    b += (long long)n_walkers * 8;                      // Philox draw counters
+    b += (long long)n_walkers * (lat_words | 1) * 4;    // lattices, odd word stride
+    b += ((long long)n_win * w + 15) / 16 * 16;         // reach
+    b += (long long)n_win * 16;                         // window state
+    b += ((long long)n_walkers + 15) / 16 * 16;         // latch
     return (int)b;
 }
 
@@ -133,184 +142,430 @@ struct Apb {
     static constexpr int value = MODEL == kIsing ? 2 : 1;
 };
 
-template <int MODEL, int G>
-__global__ void __launch_bounds__(256) sweep_kernel(DevState st, const WorkItem *items, SweepArgs args)
+// State-independent part of one trial, written by a producer warp into the
+// ring: byte offsets (from the start of the block's shared memory) of the
+// site's lattice word (Ising) or byte (Potts) and of its four neighbours'
+// (left, right, up, down); `aux` packs the bit positions of site, left and
+// right neighbour (Ising: x | x_l << 8 | x_r << 16, also as masks mx, ml,
+// mr) or the proposal offset (Potts: new value = old + aux mod q), and in
+// bit 24 the flag `near`: the
+// previous trial of the walker touched this trial's site or a neighbour (or
+// it is unknown), so values read before the previous move may be stale.
+// `lam` is the acceptance threshold.
+struct __align__(16) Trial {
+    uint32_t a_s, a_l, a_r, a_u, a_d, aux;
+    long long lam;
+    uint32_t mx, ml, mr, pad;   // Ising: bit masks of site (and up/down), left, right
+};
+
+static constexpr uint32_t kNear = 1u << 24;
+static_assert(sizeof(Trial) == 48, "ring records are 48 bytes");
+
+__device__ __forceinline__ bool site_near(int prev, int site, const Site &s, int L)
+{
+    return prev == site || prev == s.y * L + s.xl || prev == s.y * L + s.xr || prev == s.yu * L + s.x ||
+           prev == s.yd * L + s.x;
+}
+
+// The APB trials of one Philox block.  The first trial's `near` flag is set
+// (predecessor unknown) and cleared by the caller once the predecessor is
+// known; *first / *last receive the block's first and last sites.
+template <int MODEL>
+__device__ __forceinline__ void make_trials(Trial *out, unsigned long long blk, uint32_t c2, const InstDev &I,
+                                            uint32_t lat_off, int *first, int *last)
+{
+    int prev = -1;
+    const u32x4 r = philox10((uint32_t)blk, (uint32_t)(blk >> 32), c2, 0u, I.key0, I.key1);
+    if (MODEL == kIsing) {
+        const uint32_t rs[2] = {r.x, r.z}, ru[2] = {r.y, r.w};
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int site = (int)scale_u32(rs[k], (uint32_t)I.N);
+            const Site s = site_of(site, I.L, I.magic_L);
+            const uint32_t row = lat_off + 4u * (uint32_t)(s.y * I.wpr);
+            const uint32_t hx = 4u * (uint32_t)(s.x >> 5);
+            Trial t;
+            t.a_s = row + hx;
+            t.a_l = row + 4u * (uint32_t)(s.xl >> 5);
+            t.a_r = row + 4u * (uint32_t)(s.xr >> 5);
+            t.a_u = lat_off + 4u * (uint32_t)(s.yu * I.wpr) + hx;
+            t.a_d = lat_off + 4u * (uint32_t)(s.yd * I.wpr) + hx;
+            const bool near = prev < 0 || site_near(prev, site, s, I.L);
+            t.aux = (uint32_t)(s.x & 31) | ((uint32_t)(s.xl & 31) << 8) | ((uint32_t)(s.xr & 31) << 16) |
+                    (near ? kNear : 0u);
+            t.mx = 1u << (s.x & 31);
+            t.ml = 1u << (s.xl & 31);
+            t.mr = 1u << (s.xr & 31);
+            t.pad = 0u;
+            t.lam = lam_threshold(ru[k] >> 8);
+            out[k] = t;
+            if (k == 0) *first = site;
+            prev = site;
+        }
+        *last = prev;
+    } else {
+        const int site = (int)scale_u32(r.x, (uint32_t)I.N);
+        const Site s = site_of(site, I.L, I.magic_L);
+        const uint32_t L = (uint32_t)I.L;
+        Trial t;
+        t.a_s = lat_off + (uint32_t)site;
+        t.a_l = lat_off + (uint32_t)s.y * L + (uint32_t)s.xl;
+        t.a_r = lat_off + (uint32_t)s.y * L + (uint32_t)s.xr;
+        t.a_u = lat_off + (uint32_t)s.yu * L + (uint32_t)s.x;
+        t.a_d = lat_off + (uint32_t)s.yd * L + (uint32_t)s.x;
+        const bool near = prev < 0 || site_near(prev, site, s, I.L);
+        t.aux = (1u + scale_u32(r.y, (uint32_t)(I.q - 1))) | (near ? kNear : 0u);
+        t.mx = t.ml = t.mr = t.pad = 0u;
+        t.lam = lam_threshold(r.z >> 8);
+        out[0] = t;
+        *first = site;
+        *last = site;
+    }
+}
+
+// Lattice words (Ising) or values (Potts) a trial reads: site, left, right, up, down.
+struct Nbr {
+    uint32_t s, l, r, u, d;
+};
+
+template <int MODEL>
+__device__ __forceinline__ Nbr load_nbr(const unsigned char *smem, const Trial &t)
+{
+    Nbr n;
+    if (MODEL == kIsing) {
+        n.s = *reinterpret_cast<const uint32_t *>(smem + t.a_s);
+        n.l = *reinterpret_cast<const uint32_t *>(smem + t.a_l);
+        n.r = *reinterpret_cast<const uint32_t *>(smem + t.a_r);
+        n.u = *reinterpret_cast<const uint32_t *>(smem + t.a_u);
+        n.d = *reinterpret_cast<const uint32_t *>(smem + t.a_d);
+    } else {
+        n.s = smem[t.a_s];
+        n.l = smem[t.a_l];
+        n.r = smem[t.a_r];
+        n.u = smem[t.a_u];
+        n.d = smem[t.a_d];
+    }
+    return n;
+}
+
+// Bin change of a trial from the lattice values it reads.  Ising: flipping
+// s_i changes E by 2 s_i sum_j s_j = 8 - 4 (#neighbours unlike s_i), i.e.
+// 2 - #unlike bins of 4; the three in-row bits (left, right, up) sit at
+// distinct positions and are counted with one population count.  Potts
+// (Eq. (2)): (#neighbours equal to the old value) - (#equal to the new value).
+template <int MODEL>
+__device__ __forceinline__ int bin_change(const Nbr &n, const Trial &t, int q)
+{
+    if (MODEL == kIsing) {
+        const uint32_t S = (n.s & t.mx) ? 0xFFFFFFFFu : 0u;
+        const uint32_t row3 = ((n.l ^ S) & t.ml) | ((n.r ^ S) & t.mr) | ((n.u ^ S) & t.mx);
+        return 2 - __popc(row3) - __popc((n.d ^ S) & t.mx);
+    } else {
+        const int old = (int)n.s;
+        int nv = old + (int)(t.aux & 0xFFFFu);
+        nv -= nv >= q ? q : 0;
+        const int a = (int)n.l, b = (int)n.r, c = (int)n.u, d = (int)n.d;
+        return ((a == old) + (b == old) + (c == old) + (d == old)) - ((a == nv) + (b == nv) + (c == nv) + (d == nv));
+    }
+}
+
+// Predicated stores and reductions without branches.
+__device__ __forceinline__ void st_shared_u32_if(bool p, uint32_t addr, uint32_t v)
+{
+    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.shared.u32 [%1], %2;\n}" ::"r"((uint32_t)p),
+                 "r"(addr), "r"(v)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_shared_u8_if(bool p, uint32_t addr, uint32_t v)
+{
+    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.shared.u8 [%1], %2;\n}" ::"r"((uint32_t)p),
+                 "r"(addr), "r"(v)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_shared_s64_if(bool p, uint32_t addr, long long v)
+{
+    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.shared.s64 [%1], %2;\n}" ::"r"((uint32_t)p),
+                 "r"(addr), "l"(v)
+                 : "memory");
+}
+
+__device__ __forceinline__ void red_add_global_u32_if(bool p, uint32_t *ptr)
+{
+    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q red.relaxed.gpu.global.add.u32 [%1], 1;\n}" ::"r"(
+                     (uint32_t)p),
+                 "l"(ptr)
+                 : "memory");
+}
+
+__device__ __forceinline__ void named_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ void named_arrive(int id, int nthreads)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+enum : int { kBarFull = 1, kBarEmpty = 3 };  // ids 1, 2 (full) and 3, 4 (empty); 0 is __syncthreads
+
+// One thread block = n_win whole windows (nw = n_win * m <= 32 walkers).
+// Warp 0 is the consumer: lane t resolves walker t's trials in order.  Warps
+// 1..P are producers: they draw the Philox blocks and fill the ring with the
+// state-independent parts of each trial, one round (kR trials per walker)
+// ahead of the consumer, handing slots over with named barriers.  The
+// consumer keeps the trial chain short: the next trial's lattice values are
+// read one trial ahead and its bin change is computed for both outcomes of
+// the current trial; ln g of the reachable bins is read before the bin change
+// is known; H is counted in global memory with fire-and-forget reductions.
+template <int MODEL>
+__global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkItem *items, SweepArgs args)
 {
     constexpr int APB = Apb<MODEL>::value;
-    constexpr int A = APB * G;                      // trials per round and walker
     extern __shared__ __align__(16) unsigned char smem[];
     const WorkItem it = items[blockIdx.x];
     const InstDev I = st.inst[it.inst];
     const int m = I.m, w = I.w, n_win = it.n_win;
-    const int nw = n_win * m;                       // walkers in this block
-    const int tid = threadIdx.x;
-    const int g = tid % G;                          // lane within the walker group
-    const int t = tid / G;                          // walker within the block
-    const bool valid = t < nw;
-    const int tv = valid ? t : 0;                   // padding lanes shadow walker 0
+    const int nw = n_win * m;
+    const int tid = threadIdx.x, nthreads = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int n_prod = nthreads - 32;
+    const bool consumer = warp == 0;
+    const bool valid = consumer && lane < nw;
+    const int tv = (consumer && lane < nw) ? lane : 0;
     const int lw = I.lat_words;
+    const int lwp = lw | 1;                 // odd word stride spreads walkers over banks
+    const int wg = w + 2 * kGuard;
 
-    long long *lng_s = reinterpret_cast<long long *>(smem);
-    uint32_t *H_s = reinterpret_cast<uint32_t *>(lng_s + (size_t)nw * w);
-    uint32_t *lat_s = H_s + (size_t)nw * w;
-    uint8_t *reach_s = reinterpret_cast<uint8_t *>(lat_s + (size_t)nw * lw);
+    Trial *ring = reinterpret_cast<Trial *>(smem);
+    long long *lng_s = reinterpret_cast<long long *>(ring + 2 * nw * kR);
+    unsigned long long *draw_s = reinterpret_cast<unsigned long long *>(lng_s + (size_t)nw * wg);
+    uint32_t *lat_s = reinterpret_cast<uint32_t *>(draw_s + nw);
+    uint8_t *reach_s = reinterpret_cast<uint8_t *>(lat_s + (size_t)nw * lwp);
     int *wst_s = reinterpret_cast<int *>(reach_s + ((size_t)n_win * w + 15) / 16 * 16);
-    int *wstage_s = wst_s;                          // [n_win]
-    int *wconv_s = wst_s + n_win;                   // [n_win]
-    int *wmerge_s = wst_s + 2 * n_win;              // [n_win]
-    int *wgwin_s = wst_s + 3 * n_win;               // [n_win]
+    int *wstage_s = wst_s;
+    int *wconv_s = wst_s + n_win;
+    int *wmerge_s = wst_s + 2 * n_win;
+    int *wgwin_s = wst_s + 3 * n_win;
     uint8_t *latch_s = reinterpret_cast<uint8_t *>(wst_s + 4 * n_win);
 
     const int slot_base = I.slot0 + it.win_begin * m;
+    uint32_t *Hblk = st.H + I.lng_off + (long long)it.win_begin * m * w;   // this block's histograms
     // ---- load state into shared memory
-    for (int i = tid; i < nw * w; i += blockDim.x) {
-        const int k = i / w, b = i - k * w;
-        const long long off = I.lng_off + (long long)(it.win_begin * m + k) * w + b;
-        lng_s[i] = st.lng[off];
-        H_s[i] = st.H[off];
+    for (int i = tid; i < nw * wg; i += nthreads) {
+        const int k = i / wg, bb = i - k * wg - kGuard;
+        long long v = 0;
+        if (bb >= 0 && bb < w) v = st.lng[I.lng_off + (long long)(it.win_begin * m + k) * w + bb];
+        lng_s[i] = v;
     }
-    for (int i = tid; i < nw * lw; i += blockDim.x) {
+    for (int i = tid; i < nw * lw; i += nthreads) {
         const int k = i / lw, x = i - k * lw;
-        const int c = st.cfg[slot_base + k];
-        lat_s[i] = st.lat[I.lat_off + (long long)c * lw + x];
+        lat_s[k * lwp + x] = st.lat[I.lat_off + (long long)st.cfg[slot_base + k] * lw + x];
     }
-    for (int i = tid; i < n_win * w; i += blockDim.x) {
-        const int wl = i / w, b = i - wl * w;
-        const int gwin = I.win0 + it.win_begin + wl;
-        reach_s[i] = st.reach[I.reach_off + st.lo[gwin] + b];
+    for (int i = tid; i < n_win * w; i += nthreads) {
+        const int wl = i / w, bb = i - wl * w;
+        reach_s[i] = st.reach[I.reach_off + st.lo[I.win0 + it.win_begin + wl] + bb];
     }
-    for (int i = tid; i < n_win; i += blockDim.x) {
+    for (int i = tid; i < n_win; i += nthreads) {
         const int gwin = I.win0 + it.win_begin + i;
         wgwin_s[i] = gwin;
         wstage_s[i] = st.stage[gwin];
         wconv_s[i] = st.conv[gwin];
         wmerge_s[i] = 0;
     }
-    for (int i = tid; i < nw; i += blockDim.x) latch_s[i] = st.latch[slot_base + i];
+    for (int i = tid; i < nw; i += nthreads) {
+        latch_s[i] = st.latch[slot_base + i];
+        draw_s[i] = st.draw[slot_base + i];
+    }
     __syncthreads();
 
-    const int wl = tv / m, j = tv - wl * m;          // window within block, walker within window
-    const int slot = slot_base + tv;
-    const int lo = st.lo[I.win0 + it.win_begin + wl];
-    const int hi = lo + w - 1;
-    int b = st.bin[slot];
-    int E = st.E[slot];
-    unsigned long long draw = st.draw[slot];
+    // consumer state (lane tv)
+    const int wl_c = tv / m;
+    const int lo = st.lo[I.win0 + it.win_begin + wl_c];
+    int b = st.bin[slot_base + tv];
+    long long *lng = lng_s + (size_t)tv * wg + kGuard - lo;   // indexed by global bin
+    uint32_t *H = Hblk + (size_t)tv * w - lo;                  // global, indexed by global bin
+    const int q = I.q, N = I.N;
+    const int rounds = (N + kR - 1) / kR;
     unsigned long long n_acc = 0;
-    long long *lng = lng_s + (size_t)tv * w - lo;     // indexed by global bin
-    uint32_t *H = H_s + (size_t)tv * w - lo;
-    uint32_t *lat = lat_s + (size_t)tv * lw;
-    const uint32_t c2 = ((uint32_t)(it.win_begin + wl) << 16) | (uint32_t)j;
-    const int L = I.L, N = I.N, wpr = I.wpr, q = I.q;
-    const bool leader = (g == 0) && valid;
+    const uint32_t lat_base = (uint32_t)(reinterpret_cast<unsigned char *>(lat_s) - smem);
     const unsigned long long sweep0 = st.counters[0];
-    const int rounds = N / A;                        // N is a multiple of A (checked on the host)
 
     for (long sw = 0; sw < args.n_sweeps; ++sw) {
-        const bool frozen = wconv_s[wl] != 0;
-        const long long lnf = frozen ? 0 : (1LL << (32 - wstage_s[wl]));
-        for (int rd = 0; rd < rounds; ++rd) {
-            // ---- every lane: one Philox block and its state-independent parts
-            const unsigned long long blk = draw + (unsigned long long)(rd * G + g);
-            const u32x4 r = philox10((uint32_t)blk, (uint32_t)(blk >> 32), c2, 0u, I.key0, I.key1);
-            int my_site[APB];
-            int my_prop[APB];
-            long long my_lam[APB];
-            if (MODEL == kIsing) {
-                my_site[0] = (int)scale_u32(r.x, (uint32_t)N);
-                my_lam[0] = lam_threshold(r.y >> 8);
-                my_site[APB - 1] = (int)scale_u32(r.z, (uint32_t)N);
-                my_lam[APB - 1] = lam_threshold(r.w >> 8);
-                my_prop[0] = my_prop[APB - 1] = 0;
-            } else {
-                my_site[0] = (int)scale_u32(r.x, (uint32_t)N);
-                my_prop[0] = 1 + (int)scale_u32(r.y, (uint32_t)(q - 1));
-                my_lam[0] = lam_threshold(r.z >> 8);
-            }
-            // ---- gather the group's A trials into the leader (warp-wide)
-            int site_a[A];
-            int prop_a[A];
-            long long lam_a[A];
+        if (!consumer) {
+            // ---------------- producers ----------------
+            const int ptid = tid - 32;
+            for (int k = 0; k < rounds; ++k) {
+                const int slot = k & 1;
+                if (k >= 2) named_sync(kBarEmpty + slot, nthreads);
+                const int cnt = min(kR, N - k * kR);
+                const int nblk = cnt / APB;
+                const int total = nw * nblk;
+                for (int base = 0; base < total; base += n_prod) {
+                    const int task = base + ptid;
+                    const bool act = task < total;
+                    const int tk = act ? task : total - 1;
+                    // walker-fastest task order: consecutive lanes write
+                    // consecutive records of the ring (no bank conflicts)
+                    const int bi = tk / nw, wk = tk - bi * nw;
+                    const int wlk = wk / m, jk = wk - wlk * m;
+                    const uint32_t c2 = ((uint32_t)(it.win_begin + wlk) << 16) | (uint32_t)jk;
+                    const unsigned long long blk = draw_s[wk] + (unsigned long long)(k * (kR / APB) + bi);
+                    Trial tr[APB];
+                    int first, last;
+                    make_trials<MODEL>(tr, blk, c2, I, lat_base + 4u * (uint32_t)(wk * lwp), &first, &last);
+                    // the trial before the block's first one is the last trial of
+                    // the lane nw below, which holds the walker's previous block
+                    // when it is in the same warp and pass
+                    const int from_left = __shfl_up_sync(0xffffffffu, last, nw < 32 ? nw : 0);
+                    if (nw < 32 && lane >= nw && bi > 0) {
+                        const Site fs = site_of(first, I.L, I.magic_L);
+                        if (!site_near(from_left, first, fs, I.L)) tr[0].aux &= ~kNear;
+                    }
+                    if (act) {
+                        // ring layout [slot][trial][walker]: the consumer lanes
+                        // read consecutive records, free of bank conflicts
+                        Trial *dst = ring + ((size_t)slot * kR + bi * APB) * nw + wk;
 #pragma unroll
-            for (int a = 0; a < A; ++a) {
-                const int src_lane = a / APB;
-                const int which = a % APB;
-                if (G == 1) {
-                    site_a[a] = my_site[which];
-                    prop_a[a] = my_prop[which];
-                    lam_a[a] = my_lam[which];
-                } else {
-                    const int lane0 = (threadIdx.x & 31) - g;
-                    site_a[a] = __shfl_sync(0xffffffffu, my_site[which], lane0 + src_lane);
-                    prop_a[a] = __shfl_sync(0xffffffffu, my_prop[which], lane0 + src_lane);
-                    lam_a[a] = __shfl_sync(0xffffffffu, my_lam[which], lane0 + src_lane);
+                        for (int i = 0; i < APB; ++i) dst[(size_t)i * nw] = tr[i];
+                    }
                 }
+                named_arrive(kBarFull + slot, nthreads);
             }
-            // ---- the leader resolves the trials in order (Sec. II A)
-            if (leader) {
-#pragma unroll
-                for (int a = 0; a < A; ++a) {
-                    const int site = site_a[a];
-                    const Site s = site_of(site, L, I.magic_L);
-                    int db, nv = 0;
+        } else {
+            // ---------------- consumer ----------------
+            const bool frozen = wconv_s[wl_c] != 0;
+            const long long lnf = frozen ? 0 : (1LL << (32 - wstage_s[wl_c]));
+            long long cur = lng[b];
+            uint32_t acc_count = 0;
+            const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+            // shared address of ln g of global bin 0 of this walker (bins lo..hi valid)
+            const uint32_t lng_sa = (uint32_t)__cvta_generic_to_shared(lng_s + (size_t)tv * wg + kGuard) - 8u * (uint32_t)lo;
+            for (int k = 0; k < rounds; ++k) {
+                const int slot = k & 1;
+                named_sync(kBarFull + slot, nthreads);
+                const int cnt = min(kR, N - k * kR);
+                const Trial *rr = ring + (size_t)slot * kR * nw + tv;   // record a at rr[a * nw]
+                Trial t = rr[0];
+                Trial t1 = rr[cnt > 1 ? nw : 0];
+                const Nbr n0 = load_nbr<MODEL>(smem, t);
+                int db = bin_change<MODEL>(n0, t, q);     // bin change of the current trial
+                uint32_t sv = n0.s;                        // its site word (Ising) / value (Potts)
+                bool acc_prev = false;
+#pragma unroll 3
+                for (int a = 0; a < cnt; ++a) {
+                    const Trial t2 = rr[(size_t)(a + 2 < cnt ? a + 2 : cnt - 1) * nw];
+                    // the next trial's lattice values, read before this trial's move
+                    const Nbr nn = load_nbr<MODEL>(smem, t1);
+                    // ln g of every bin a move can reach, before the move is known
+                    const long long sm1 = lng[b - 1], sp1 = lng[b + 1], sm2 = lng[b - 2], sp2 = lng[b + 2];
+                    long long sm3 = 0, sp3 = 0, sm4 = 0, sp4 = 0;
+                    if (MODEL == kPotts) {
+                        sm3 = lng[b - 3];
+                        sp3 = lng[b + 3];
+                        sm4 = lng[b - 4];
+                        sp4 = lng[b + 4];
+                    }
+                    // rare: the previous trial moved this trial's site or a
+                    // neighbour after db and sv were taken -- read them again
+                    if (acc_prev && (t.aux & kNear)) {
+                        const Nbr nf = load_nbr<MODEL>(smem, t);
+                        db = bin_change<MODEL>(nf, t, q);
+                        sv = nf.s;
+                    }
+                    // this trial's move: Ising flips one bit of the site word,
+                    // Potts writes the new value
+                    uint32_t moved;
                     if (MODEL == kIsing) {
-                        db = ising_flip_dbin(lat, wpr, s);
+                        moved = sv ^ t.mx;
                     } else {
-                        const int old = potts_get(lat, site);
-                        nv = old + prop_a[a];
-                        nv = nv >= q ? nv - q : nv;
-                        db = potts_dE(lat, L, s, old, nv);
+                        int nv = (int)sv + (int)(t.aux & 0xFFFFu);
+                        nv -= nv >= q ? q : 0;
+                        moved = (uint32_t)nv;
                     }
+                    // accept iff ln g(E') < ln g(E) + lam, i.e. with min(1, g(E)/g(E'))
                     const int bn = b + db;
-                    bool acc = false;
-                    if (bn >= lo && bn <= hi) acc = (lng[bn] - lng[b]) < lam_a[a];
-                    if (acc) {
-                        if (MODEL == kIsing) ising_flip(lat, wpr, s);
-                        else potts_set(lat, site, nv);
-                        b = bn;
-                        E += db * I.step;
-                        ++n_acc;
+                    const bool inw = (unsigned)(bn - lo) < (unsigned)w;
+                    const long long thr = cur + t.lam;
+                    long long v;
+                    if (MODEL == kIsing) {
+                        const long long p1 = db < 0 ? sm1 : sp1, p2 = db < 0 ? sm2 : sp2;
+                        v = (db & 1) ? p1 : p2;
+                    } else {
+                        const int ad = db < 0 ? -db : db;
+                        const long long p1 = db < 0 ? sm1 : sp1, p2 = db < 0 ? sm2 : sp2;
+                        const long long p3 = db < 0 ? sm3 : sp3, p4 = db < 0 ? sm4 : sp4;
+                        const long long p12 = (ad & 1) ? p1 : p2, p34 = (ad & 1) ? p3 : p4;
+                        v = ad > 2 ? p34 : p12;
                     }
-                    if (!frozen) lng[b] += lnf;
-                    H[b] += 1u;
+                    v = db == 0 ? cur : v;
+                    const bool acc = inw && (v < thr);
+                    if (MODEL == kIsing) st_shared_u32_if(valid && acc, sbase + t.a_s, moved);
+                    else st_shared_u8_if(valid && acc, sbase + t.a_s, moved);
+                    // the next trial's bin change and site word from the values
+                    // read before this move (the flag above catches the cases
+                    // where this move changes them; an Ising site word shared
+                    // with this trial's site gets the flipped bit here)
+                    const int db_next = bin_change<MODEL>(nn, t1, q);
+                    uint32_t sv_next = nn.s;
+                    if (MODEL == kIsing) sv_next ^= (acc && t1.a_s == t.a_s) ? t.mx : 0u;
+                    b = acc ? bn : b;
+                    cur = (acc ? v : cur) + lnf;
+                    acc_count += acc ? 1u : 0u;
+                    st_shared_s64_if(valid, lng_sa + 8u * (uint32_t)b, cur);
+                    red_add_global_u32_if(valid, H + b);
+                    acc_prev = acc;
+                    db = db_next;
+                    sv = sv_next;
+                    t = t1;
+                    t1 = t2;
                 }
+                if (k + 2 < rounds) named_arrive(kBarEmpty + slot, nthreads);
             }
+            n_acc += acc_count;
         }
-        draw += (unsigned long long)rounds * G;
         __syncthreads();
+        if (tid < nw) draw_s[tid] += (unsigned long long)(N / APB);
         // ---- end of sweep: flatness, merge, ln f schedule
         const unsigned long long sweeps_done = sweep0 + (unsigned long long)sw + 1ull;
         if (sweeps_done % (unsigned long long)args.check_every == 0ull) {
-            // flatness per walker: G lanes split the bins, shuffles combine
-            unsigned long long mn = ~0ull, sum = 0ull;
-            long long amax = 0;
-            const bool test = valid && !frozen && !latch_s[tv];
-            for (int bb = lo + g; bb <= hi; bb += G) {
-                const long long v = lng[bb];
-                const long long av = v < 0 ? -v : v;
-                amax = av > amax ? av : amax;
-                if (reach_s[wl * w + (bb - lo)]) {
-                    const unsigned long long hv = H[bb];
-                    mn = hv < mn ? hv : mn;
-                    sum += hv;
+            // flatness per walker: one warp per walker, lanes split the bins
+            for (int wk = warp; wk < nw; wk += nthreads / 32) {
+                const int wlk = wk / m;
+                const long long *lk = lng_s + (size_t)wk * wg + kGuard;
+                const uint32_t *hk = Hblk + (size_t)wk * w;
+                unsigned long long mn = ~0ull, sum = 0ull;
+                long long amax = 0;
+                for (int bb = lane; bb < w; bb += 32) {
+                    const long long v = lk[bb];
+                    const long long av = v < 0 ? -v : v;
+                    amax = av > amax ? av : amax;
+                    if (reach_s[wlk * w + bb]) {
+                        const unsigned long long hv = __ldcg(hk + bb);
+                        mn = hv < mn ? hv : mn;
+                        sum += hv;
+                    }
+                }
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned long long omn = __shfl_xor_sync(0xffffffffu, mn, o);
+                    const unsigned long long osm = __shfl_xor_sync(0xffffffffu, sum, o);
+                    const long long oam = __shfl_xor_sync(0xffffffffu, amax, o);
+                    mn = omn < mn ? omn : mn;
+                    sum += osm;
+                    amax = oam > amax ? oam : amax;
+                }
+                if (lane == 0) {
+                    if (amax >= (1LL << 53)) atomicOr(st.error, kErrRange);
+                    const int n_reach = st.n_reach[I.win0 + it.win_begin + wlk];
+                    if (!wconv_s[wlk] && !latch_s[wk] && (double)mn * (double)n_reach >= I.p_flat * (double)sum)
+                        latch_s[wk] = 1;
                 }
             }
-#pragma unroll
-            for (int o = 1; o < G; o <<= 1) {
-                const unsigned long long omn = __shfl_xor_sync(0xffffffffu, mn, o);
-                const unsigned long long osm = __shfl_xor_sync(0xffffffffu, sum, o);
-                const long long oam = __shfl_xor_sync(0xffffffffu, amax, o);
-                mn = omn < mn ? omn : mn;
-                sum += osm;
-                amax = oam > amax ? oam : amax;
-            }
-            if (valid && amax >= (1LL << 53)) atomicOr(st.error, kErrRange);
-            if (leader && test) {
-                const int n_reach = st.n_reach[I.win0 + it.win_begin + wl];
-                if ((double)mn * (double)n_reach >= I.p_flat * (double)sum) latch_s[tv] = 1;
-            }
             __syncthreads();
-            for (int i = tid; i < n_win; i += blockDim.x) {
+            for (int i = tid; i < n_win; i += nthreads) {
                 int all = !wconv_s[i];
                 for (int jj = 0; jj < m && all; ++jj) all = latch_s[i * m + jj];
                 wmerge_s[i] = all;
@@ -318,19 +573,19 @@ __global__ void __launch_bounds__(256) sweep_kernel(DevState st, const WorkItem 
             __syncthreads();
             // merge: ln g <- mean over the window's walkers (nearest 2^-32, ties
             // to even), H <- 0
-            for (int i = tid; i < n_win * w; i += blockDim.x) {
+            for (int i = tid; i < n_win * w; i += nthreads) {
                 const int ww = i / w, bb = i - ww * w;
                 if (!wmerge_s[ww]) continue;
-                long long s = 0;
-                for (int jj = 0; jj < m; ++jj) s += lng_s[(size_t)(ww * m + jj) * w + bb];
-                const long long mean = div_round_even(s, m);
+                long long sacc = 0;
+                for (int jj = 0; jj < m; ++jj) sacc += lng_s[(size_t)(ww * m + jj) * wg + kGuard + bb];
+                const long long mean = div_round_even(sacc, m);
                 for (int jj = 0; jj < m; ++jj) {
-                    lng_s[(size_t)(ww * m + jj) * w + bb] = mean;
-                    H_s[(size_t)(ww * m + jj) * w + bb] = 0u;
+                    lng_s[(size_t)(ww * m + jj) * wg + kGuard + bb] = mean;
+                    Hblk[(size_t)(ww * m + jj) * w + bb] = 0u;
                 }
             }
             __syncthreads();
-            for (int i = tid; i < n_win; i += blockDim.x) {
+            for (int i = tid; i < n_win; i += nthreads) {
                 if (!wmerge_s[i]) continue;
                 for (int jj = 0; jj < m; ++jj) latch_s[i * m + jj] = 0;
                 if (wstage_s[i] >= I.stage_final) {
@@ -341,68 +596,50 @@ __global__ void __launch_bounds__(256) sweep_kernel(DevState st, const WorkItem 
                 }
                 wmerge_s[i] = 0;
             }
-            __syncthreads();
         }
+        __syncthreads();
     }
 
     // ---- write back
-    if (leader) {
-        st.bin[slot] = b;
-        st.E[slot] = E;
-        st.draw[slot] = draw;
-        st.n_acc[slot] += n_acc;
+    if (valid) {
+        st.bin[slot_base + tv] = b;
+        st.E[slot_base + tv] = (int)(I.e_min + (long long)b * I.step);
+        st.n_acc[slot_base + tv] += n_acc;
     }
-    __syncthreads();
-    for (int i = tid; i < nw * w; i += blockDim.x) {
+    for (int i = tid; i < nw * w; i += nthreads) {
         const int k = i / w, bb = i - k * w;
-        const long long off = I.lng_off + (long long)(it.win_begin * m + k) * w + bb;
-        st.lng[off] = lng_s[i];
-        st.H[off] = H_s[i];
+        st.lng[I.lng_off + (long long)(it.win_begin * m) * w + i] = lng_s[(size_t)k * wg + kGuard + bb];
     }
-    for (int i = tid; i < nw * lw; i += blockDim.x) {
+    for (int i = tid; i < nw * lw; i += nthreads) {
         const int k = i / lw, x = i - k * lw;
-        const int c = st.cfg[slot_base + k];
-        st.lat[I.lat_off + (long long)c * lw + x] = lat_s[i];
+        st.lat[I.lat_off + (long long)st.cfg[slot_base + k] * lw + x] = lat_s[k * lwp + x];
     }
-    for (int i = tid; i < n_win; i += blockDim.x) {
+    for (int i = tid; i < n_win; i += nthreads) {
         st.stage[wgwin_s[i]] = wstage_s[i];
         st.conv[wgwin_s[i]] = (uint8_t)wconv_s[i];
     }
-    for (int i = tid; i < nw; i += blockDim.x) st.latch[slot_base + i] = latch_s[i];
-}
-
-template <int MODEL, int G>
-static cudaError_t launch_sweep_t(const DevState &st, const SweepLaunch &sl, SweepArgs a,
-                                  cudaStream_t s)
-{
-    sweep_kernel<MODEL, G><<<sl.n_items, sl.threads, sl.smem, s>>>(st, sl.items, a);
-    return cudaGetLastError();
-}
-
-template <int MODEL, int G>
-static cudaError_t prepare_t(int smem)
-{
-    return cudaFuncSetAttribute(sweep_kernel<MODEL, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-}
-
-int prepare_sweep(int model, int lanes, int smem)
-{
-    cudaError_t e = cudaErrorInvalidValue;
-    if (model == kIsing) {
-        switch (lanes) {
-            case 1: e = prepare_t<kIsing, 1>(smem); break;
-            case 2: e = prepare_t<kIsing, 2>(smem); break;
-            case 4: e = prepare_t<kIsing, 4>(smem); break;
-            case 8: e = prepare_t<kIsing, 8>(smem); break;
-        }
-    } else {
-        switch (lanes) {
-            case 1: e = prepare_t<kPotts, 1>(smem); break;
-            case 2: e = prepare_t<kPotts, 2>(smem); break;
-            case 4: e = prepare_t<kPotts, 4>(smem); break;
-            case 8: e = prepare_t<kPotts, 8>(smem); break;
-        }
+    for (int i = tid; i < nw; i += nthreads) {
+        st.latch[slot_base + i] = latch_s[i];
+        st.draw[slot_base + i] = draw_s[i];
     }
+}
+
+int prepare_sweep(int model, int producers, int smem)
+{
+    (void)producers;
+    // the attribute belongs to the kernel, not to a context: never lower it
+    // below what another live context already needs
+    static int granted[2] = {0, 0};
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    if (smem <= granted[model & 1]) return 0;
+    granted[model & 1] = smem;
+    // every launch of the kernel asks for the largest shared-memory carveout, so
+    // launches of different size classes can share an SM
+    const void *fn = model == kIsing ? (const void *)sweep_kernel<kIsing> : (const void *)sweep_kernel<kPotts>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     return (int)e;
 }
 
@@ -410,23 +647,10 @@ int launch_sweeps(const DevState &st, const SweepLaunch &sl, long n_sweeps, long
 {
     SweepArgs a{n_sweeps, check_every};
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = cudaErrorInvalidValue;
-    if (sl.model == kIsing) {
-        switch (sl.lanes) {
-            case 1: e = launch_sweep_t<kIsing, 1>(st, sl, a, s); break;
-            case 2: e = launch_sweep_t<kIsing, 2>(st, sl, a, s); break;
-            case 4: e = launch_sweep_t<kIsing, 4>(st, sl, a, s); break;
-            case 8: e = launch_sweep_t<kIsing, 8>(st, sl, a, s); break;
-        }
-    } else {
-        switch (sl.lanes) {
-            case 1: e = launch_sweep_t<kPotts, 1>(st, sl, a, s); break;
-            case 2: e = launch_sweep_t<kPotts, 2>(st, sl, a, s); break;
-            case 4: e = launch_sweep_t<kPotts, 4>(st, sl, a, s); break;
-            case 8: e = launch_sweep_t<kPotts, 8>(st, sl, a, s); break;
-        }
-    }
-    return (int)e;
+    if (sl.threads < 64 || sl.threads > 160 || sl.threads % 32 || sl.max_walkers > 32) return (int)cudaErrorInvalidValue;
+    if (sl.model == kIsing) sweep_kernel<kIsing><<<sl.n_items, sl.threads, sl.smem, s>>>(st, sl.items, a);
+    else sweep_kernel<kPotts><<<sl.n_items, sl.threads, sl.smem, s>>>(st, sl.items, a);
+    return (int)cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -1,27 +1,36 @@
-// rewl_tune.cu -- launch-shape choice for the sweep kernel: lanes per walker
-// (G) and windows per thread block, per size class.  Never changes results:
-// every random number is keyed by (instance, window, walker, draw index), and
-// walkers of one window always share a block.
+// rewl_tune.cu -- launch-shape choice for the sweep kernel: windows per thread
+// block (walkers per consumer warp) and producer warps per block, per size
+// class.  Never changes results: every random number is keyed by (instance,
+// window, walker, draw index), walkers of one window always share a block, and
+// each walker's trials are resolved in draw order by one consumer lane.
 #include <algorithm>
 
 #include "rewl_internal.h"
 
 namespace rewl {
 
-static const int kSMs = 152;             // GB300
-static const int kSmemBudget = 110 * 1024;  // two blocks per SM
-static const int kMaxThreads = 256;
+static const int kSMs = 152;                 // GB300
+static const int kSmemBudget = 110 * 1024;   // leaves room for two blocks per SM
 
-// Lanes per walker: with few walkers per SM the per-walker dependency chain
-// bounds throughput, so more lanes take over the state-independent work
-// (Philox, thresholds); with many walkers one lane per walker issues fewest
-// instructions per trial.
-static int pick_lanes(int total_walkers, int model, int N, int m)
+// Walkers per block: with few walkers per SM the per-walker dependency chain
+// bounds throughput and small blocks spread walkers over all SMs; with many
+// walkers, full consumer warps issue fewest instructions per trial.
+static int pick_walkers(int total_walkers)
 {
-    const int apb = model == kIsing ? 2 : 1;
-    int lanes = total_walkers <= kSMs * 32 ? 4 : (total_walkers <= kSMs * 96 ? 2 : 1);
-    while (lanes > 1 && (N % (apb * lanes) != 0 || m * lanes > kMaxThreads)) lanes /= 2;
-    return lanes;
+    if (total_walkers <= kSMs * 32) return 8;
+    if (total_walkers <= kSMs * 96) return 16;
+    return 32;
+}
+
+// Producer warps: Philox and threshold work per trial is ~1.5 (Ising) to ~2.5
+// (Potts) times the consumer's per-trial work; one producer lane serves one
+// Philox block per round.
+static int pick_producers(int model, int nw)
+{
+    const int per8 = model == kIsing ? 1 : 1;
+    int p = (nw + 7) / 8 * per8;
+    if (model == kPotts) p = (nw + 5) / 6;
+    return std::max(1, std::min(4, p));
 }
 
 int autotune_plan(rewl_ctx *ctx)
@@ -31,20 +40,16 @@ int autotune_plan(rewl_ctx *ctx)
     for (int c = 0; c < nc; ++c) {
         int model, N, w, m, lw;
         class_shape(ctx, c, &model, &N, &w, &m, &lw);
-        const int apb = model == kIsing ? 2 : 1;
-        int lanes = forced_lanes(ctx) ? forced_lanes(ctx) : pick_lanes(tot, model, N, m);
-        if (N % (apb * lanes) != 0 || m * lanes > kMaxThreads) return 1;
-        const int per_win = sweep_smem_bytes(m, 1, w, lw);
-        if (per_win > 227 * 1024) return 1;
+        if (m > 32) return 1;
+        if (sweep_smem_bytes(m, 1, w, lw) > 227 * 1024) return 1;
         int wpc = forced_wpc(ctx);
         if (!wpc) {
-            wpc = std::max(1, 32 / (m * lanes));
-            while (wpc > 1 && (sweep_smem_bytes(wpc * m, wpc, w, lw) > kSmemBudget ||
-                               wpc * m * lanes > kMaxThreads))
-                --wpc;
+            wpc = std::max(1, pick_walkers(tot) / m);
+            while (wpc > 1 && (wpc * m > 32 || sweep_smem_bytes(wpc * m, wpc, w, lw) > kSmemBudget)) --wpc;
         }
-        if (sweep_smem_bytes(wpc * m, wpc, w, lw) > 227 * 1024 || wpc * m * lanes > kMaxThreads) return 1;
-        plan_class(ctx, c, wpc, lanes);
+        if (wpc * m > 32 || sweep_smem_bytes(wpc * m, wpc, w, lw) > 227 * 1024) return 1;
+        const int prod = forced_producers(ctx) ? forced_producers(ctx) : pick_producers(model, wpc * m);
+        plan_class(ctx, c, wpc, prod);
     }
     return 0;
 }

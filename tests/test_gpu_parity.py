@@ -94,28 +94,28 @@ def test_trajectory_matches_oracle(name, d, sweeps, cycles):
         assert_same_state(gpu, 0, orc, f"{name} cycle {c}")
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
-@pytest.mark.parametrize("wpc", [1, 3])
-def test_launch_shape_does_not_change_results(lanes, wpc):
+@pytest.mark.parametrize("producers", [1, 2, 4])
+@pytest.mark.parametrize("wpc", [1, 3, 6])
+def test_launch_shape_does_not_change_results(producers, wpc):
     d = _ising(16, 6, 2, seed=11)
-    gpu = make_gpu([d], lanes_per_walker=lanes, windows_per_cta=wpc)
+    gpu = make_gpu([d], producer_warps=producers, windows_per_cta=wpc)
     orc = make_oracle(d)
     orc.init()
     for c in range(3):
         step_both(gpu, [orc], 25)
-    assert_same_state(gpu, 0, orc, f"lanes={lanes} wpc={wpc}")
+    assert_same_state(gpu, 0, orc, f"producers={producers} wpc={wpc}")
 
 
-def test_potts_lanes_and_check_every():
+def test_potts_producers_and_check_every():
     d = _potts(16, 10, 8, 4, seed=12)
-    for lanes, ce in [(1, 1), (4, 3), (8, 1)]:
-        gpu = make_gpu([d], lanes_per_walker=lanes, check_every=ce)
+    for producers, ce in [(1, 1), (3, 3), (4, 1)]:
+        gpu = make_gpu([d], producer_warps=producers, check_every=ce)
         orc = make_oracle(d)
         orc.set_check_every(ce)
         orc.init()
         for c in range(3):
             step_both(gpu, [orc], 20)
-        assert_same_state(gpu, 0, orc, f"lanes={lanes} check_every={ce}")
+        assert_same_state(gpu, 0, orc, f"producers={producers} check_every={ce}")
 
 
 def test_batch_of_mixed_instances_matches_each_oracle():
