@@ -182,6 +182,43 @@ const char *rewl_last_error(const rewl_ctx *ctx);
 /* Release device memory, graphs and the stream the library created. */
 void rewl_destroy(rewl_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start (not part of the paper's method): a 5 -> 128 -> 128 ->
+ * 128 -> 1 perceptron with tanh hidden units predicting the entropy density
+ * s = ln g(E) / N from x = (model, 16/L, log10 q, E/N, window / (h-1)).
+ * BF16 tensor-core products with FP32 accumulation; FP32 master weights;
+ * trained with the mean squared error (loss = mean (y - t)^2 / 2) and Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8).  It only sets the starting ln g and ln f
+ * of Wang-Landau, which then corrects any error of the prediction.
+ * Parameter vector (33921 floats): W1 [128x5], b1, W2 [128x128], b2,
+ * W3 [128x128], b3, W4 [1x128], b4, W[out][in].
+ * x, t, y below are device pointers; n is a multiple of 64, n <= max_batch.
+ * ------------------------------------------------------------------------ */
+typedef struct rewl_mlp rewl_mlp;
+
+/* Allocate a network with scratch for batches of up to max_batch samples
+ * (multiple of 64); weights uniform(+-1/sqrt(fan_in)) from Philox(seed). */
+rewl_status rewl_mlp_create(rewl_mlp **out, int max_batch, unsigned long long seed, void *cuda_stream);
+rewl_status rewl_mlp_set_params(rewl_mlp *net, const float *host_params, long n);  /* resets Adam */
+rewl_status rewl_mlp_get_params(rewl_mlp *net, float *host_params, long n);
+/* y[n] = network(x[n][5]). */
+rewl_status rewl_mlp_forward(rewl_mlp *net, const float *x, float *y, int n);
+/* Gradient of the loss over the batch (host out, 33921 floats) and the loss. */
+rewl_status rewl_mlp_gradient(rewl_mlp *net, const float *x, const float *t, int n, float *grad_host,
+                              float *loss_host);
+/* One Adam step on the batch; loss_host (may be NULL) receives the loss
+ * before the step. */
+rewl_status rewl_mlp_train_step(rewl_mlp *net, const float *x, const float *t, int n, float lr,
+                                float *loss_host);
+long rewl_mlp_launch_count(const rewl_mlp *net);
+const char *rewl_mlp_last_error(const rewl_mlp *net);
+void rewl_mlp_destroy(rewl_mlp *net);
+
+/* Warm start of instance `inst`: every walker of window i gets
+ * ln g(E) = N s(E) (shifted so the window's smallest realisable value is 0,
+ * rounded to 2^-32), H = 0, and ln f = ln_f_start (a power of two; 0 freezes). */
+rewl_status rewl_warm_start(rewl_ctx *ctx, int inst, rewl_mlp *net, double ln_f_start);
+
 /* Primitive checks (device, for tests).  Acceptance thresholds
  * lam(k) = max(1, trunc(2^32 * -ln((k + 1) 2^-24))) evaluated by the device
  * routine, and Philox4x32-10 blocks for (key, counters).  k, ctr, out: device

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librewl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["rewl_kernels.cu", "rewl_api.cu", "rewl_tune.cu"]
+SOURCES = ["rewl_kernels.cu", "rewl_api.cu", "rewl_tune.cu", "rewl_mlp.cu"]
 
 
 def _nvcc():

@@ -830,6 +830,26 @@ extern "C" rewl_status rewl_set_initial_lng(rewl_ctx *ctx, int inst, const doubl
     return REWL_OK;
 }
 
+extern "C" rewl_status rewl_warm_start(rewl_ctx *ctx, int inst, rewl_mlp *net, double ln_f_start)
+{
+    rewl_status s = check_inst(ctx, inst);
+    if (s) return s;
+    if (!net) return fail(ctx, REWL_EINVAL, "rewl_warm_start: network is NULL");
+    int k0 = -1;
+    if (ln_f_start != 0.0) {
+        int e = 0;
+        const double mant = std::frexp(ln_f_start, &e);
+        if (mant != 0.5 || e > 1 || e < -31) return fail(ctx, REWL_EINVAL, "ln_f_start must be 0 or 2^-k, 0 <= k <= 32");
+        k0 = 1 - e;
+    }
+    if ((s = sync_and_check(ctx))) return s;
+    const InstDev &I = ctx->inst[inst].dev;
+    std::string why;
+    const int rc = mlp_warm_start(net, ctx->st, inst, I.h, I.w, k0, why);
+    if (rc) return fail(ctx, (rewl_status)rc, "warm start: " + why);
+    return REWL_OK;
+}
+
 extern "C" rewl_status rewl_set_option(rewl_ctx *ctx, int option, long value)
 {
     if (!ctx) return REWL_EINVAL;

@@ -112,6 +112,15 @@ int launch_debug_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr, uint32_t 
 
 }  // namespace rewl
 
+// The learned warm start (rewl_mlp.cu): predict ln g of every window of an
+// instance and install it in its walkers (k0 = starting stage, -1 = frozen).
+#include <string>
+struct rewl_mlp;
+namespace rewl {
+struct DevState;
+int mlp_warm_start(rewl_mlp *net, const DevState &st, int inst, int h, int w, int k0, std::string &why);
+}  // namespace rewl
+
 // Planning hooks between the host library and the autotuner (rewl_tune.cu).
 struct rewl_ctx;
 namespace rewl {

@@ -66,12 +66,27 @@ def lib():
         L.rewl_last_error.restype = C.c_char_p
         L.rewl_destroy.argtypes = [vp]
         L.rewl_destroy.restype = None
+        L.rewl_mlp_create.argtypes = [C.POINTER(vp), i32, u64, vp]
+        L.rewl_mlp_set_params.argtypes = [vp, vp, i64]
+        L.rewl_mlp_get_params.argtypes = [vp, vp, i64]
+        L.rewl_mlp_forward.argtypes = [vp, vp, vp, i32]
+        L.rewl_mlp_gradient.argtypes = [vp, vp, vp, i32, vp, vp]
+        L.rewl_mlp_train_step.argtypes = [vp, vp, vp, i32, C.c_float, vp]
+        L.rewl_mlp_launch_count.argtypes = [vp]
+        L.rewl_mlp_launch_count.restype = i64
+        L.rewl_mlp_last_error.argtypes = [vp]
+        L.rewl_mlp_last_error.restype = C.c_char_p
+        L.rewl_mlp_destroy.argtypes = [vp]
+        L.rewl_mlp_destroy.restype = None
+        L.rewl_warm_start.argtypes = [vp, i32, vp, f64]
         L.rewl_debug_lam.argtypes = [vp, vp, i64]
         L.rewl_debug_philox.argtypes = [u32, u32, vp, vp, i64]
         for name in ("rewl_create", "rewl_create_batch", "rewl_run", "rewl_exchange", "rewl_run_cycles",
                      "rewl_run_to_convergence", "rewl_get_dos", "rewl_status_query", "rewl_set_initial_lng",
                      "rewl_geometry", "rewl_get_state", "rewl_get_counters", "rewl_set_option", "rewl_save",
-                     "rewl_load", "rewl_debug_lam", "rewl_debug_philox"):
+                     "rewl_load", "rewl_debug_lam", "rewl_debug_philox", "rewl_mlp_create", "rewl_mlp_set_params",
+                     "rewl_mlp_get_params", "rewl_mlp_forward", "rewl_mlp_gradient", "rewl_mlp_train_step",
+                     "rewl_warm_start"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -196,6 +211,10 @@ class Rewl:
     def launch_count(self):
         return int(lib().rewl_launch_count(self._h))
 
+    def warm_start(self, inst, net, ln_f_start):
+        """rewl_warm_start: ln g of every walker from the network, ln f = ln_f_start."""
+        _check(lib().rewl_warm_start(self._h, inst, net._h, ln_f_start), self._h)
+
     def save(self, path):
         _check(lib().rewl_save(self._h, path.encode()), self._h)
 
@@ -266,3 +285,67 @@ def debug_lam(k_dev, out_dev, n):
 
 def debug_philox(key0, key1, ctr_dev, out_dev, n):
     _check(lib().rewl_debug_philox(key0, key1, C.c_void_p(ctr_dev), C.c_void_p(out_dev), n))
+
+
+N_PARAMS = 33921
+
+
+def _mcheck(code, h):
+    if code != 0:
+        raise RewlError(code, lib().rewl_mlp_last_error(h).decode())
+
+
+class Mlp:
+    """The warm-start network (``rewl_mlp_*``).  x, t, y are torch CUDA tensors
+    (float32, contiguous); batches are multiples of 64."""
+
+    def __init__(self, max_batch=8192, seed=0, stream=None):
+        self._h = C.c_void_p()
+        code = lib().rewl_mlp_create(C.byref(self._h), max_batch, seed, _stream_ptr(stream))
+        if code != 0:
+            msg = lib().rewl_mlp_last_error(self._h if self._h else None).decode()
+            if self._h:
+                lib().rewl_mlp_destroy(self._h)
+                self._h = C.c_void_p()
+            raise RewlError(code, msg)
+        self.max_batch = max_batch
+
+    def close(self):
+        if self._h:
+            lib().rewl_mlp_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        a = np.ascontiguousarray(p, dtype=np.float32)
+        _mcheck(lib().rewl_mlp_set_params(self._h, _p(a), a.size), self._h)
+
+    def get_params(self):
+        a = np.zeros(N_PARAMS, np.float32)
+        _mcheck(lib().rewl_mlp_get_params(self._h, _p(a), a.size), self._h)
+        return a
+
+    def forward(self, x, y):
+        _mcheck(lib().rewl_mlp_forward(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.shape[0]),
+                self._h)
+
+    def gradient(self, x, t):
+        g = np.zeros(N_PARAMS, np.float32)
+        loss = np.zeros(1, np.float32)
+        _mcheck(lib().rewl_mlp_gradient(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()), x.shape[0],
+                                        _p(g), _p(loss)), self._h)
+        return g, float(loss[0])
+
+    def train_step(self, x, t, lr, want_loss=False):
+        loss = np.zeros(1, np.float32)
+        _mcheck(lib().rewl_mlp_train_step(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()), x.shape[0],
+                                          lr, _p(loss) if want_loss else None), self._h)
+        return float(loss[0]) if want_loss else None
+
+    def launch_count(self):
+        return int(lib().rewl_mlp_launch_count(self._h))

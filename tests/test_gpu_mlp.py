@@ -1,0 +1,130 @@
+"""Warm-start network on the GPU: forward and gradients against the FP64
+reference (oracle/mlp.py), training, and what the warm start gains over plain
+REWL on the same GPU at comparable ln g error."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import concat as cc
+from oracle import mlp as M
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def stream():
+    import torch
+    s = torch.cuda.Stream()
+    torch.cuda.set_stream(s)
+    yield s
+    torch.cuda.synchronize()
+
+
+def _features(n, seed):
+    rng = np.random.default_rng(seed)
+    x = np.stack([rng.integers(0, 2, n), 16.0 / rng.choice([8, 16, 32, 64], n), rng.choice([0.30103, 1.0], n),
+                  rng.uniform(-2, 2, n), rng.uniform(0, 1, n)], axis=1)
+    return x.astype(np.float32)
+
+
+def test_forward_matches_fp64_reference(stream):
+    import torch
+    from paper_1407_5140_gb300 import rewl as R
+    p = M.init_params(3).astype(np.float32)
+    net = R.Mlp(max_batch=1024, seed=1, stream=stream)
+    net.set_params(p)
+    x = _features(512, 4)
+    y = torch.empty(512, dtype=torch.float32, device="cuda")
+    net.forward(torch.from_numpy(x).cuda(), y)
+    ref, _ = M.forward(p.astype(np.float64), x.astype(np.float64))
+    got = y.cpu().numpy()
+    # BF16 operands (8-bit mantissa) in the two 128 x 128 layers, FP32 accumulation
+    assert np.max(np.abs(got - ref)) <= 2e-2 * np.max(np.abs(ref)) + 2e-3
+
+
+def test_gradient_matches_fp64_reference(stream):
+    import torch
+    from paper_1407_5140_gb300 import rewl as R
+    p = M.init_params(5).astype(np.float32)
+    net = R.Mlp(max_batch=2048, seed=1, stream=stream)
+    net.set_params(p)
+    x = _features(2048, 6)
+    t = (0.3 * np.sin(2 * x[:, 3]) + 0.1 * x[:, 1]).astype(np.float32)
+    g, loss = net.gradient(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    gref = M.gradient(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    lref = M.loss(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - lref) <= 1e-2 * lref + 1e-6
+    k = 0
+    for o, i in M.SIZES:
+        for size in (o * i, o):
+            a, b = g[k:k + size], gref[k:k + size]
+            rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
+            assert rel < 5e-2, (k, size, rel)
+            k += size
+
+
+def test_training_reduces_loss(stream):
+    import torch
+    from paper_1407_5140_gb300 import rewl as R
+    from paper_1407_5140_gb300 import warmstart as WS
+    net = R.Mlp(max_batch=4096, seed=7, stream=stream)
+    x = _features(16384, 8)
+    t = (0.4 * np.tanh(1.5 * x[:, 3]) + 0.2 * x[:, 0] * x[:, 3] ** 2 + 0.05 * x[:, 1]).astype(np.float32)
+    hist = WS.train(net, x, t, steps=600, batch=2048, lr=3e-3, seed=1, log_every=100)
+    assert hist[-1][1] < hist[0][1] / 30, hist
+
+
+def _golden(L):
+    rows = np.loadtxt(os.path.join(GOLDEN, f"ising_L{L}_exact_lng.txt"), usecols=(0, 1))
+    N = L * L
+    out = np.full(N + 1, np.nan)
+    for E, lg in rows:
+        out[(int(E) + 2 * N) // 4] = lg
+    return out
+
+
+def test_warm_start_cuts_sweeps_at_comparable_error(stream):
+    """Train on plain-REWL ln g of small lattices (Ising L = 8, 12 and q=10
+    Potts L = 8), then start Ising L = 16 from the prediction at ln f = 2^-4
+    and compare the sweeps of the slowest window (Eq. (7)'s MC time) and the
+    error against the exact DOS with plain REWL from ln g = 0, ln f = 1."""
+    from paper_1407_5140_gb300 import rewl as R
+    from paper_1407_5140_gb300 import warmstart as WS
+    from paper_1407_5140_gb300 import workloads as W
+
+    train_inst = [W._inst(R.ISING, 8, 2, 4, 2, 100 + s, ln_f_final=2.0 ** -14) for s in range(2)] + \
+                 [W._inst(R.ISING, 12, 2, 4, 2, 200 + s, ln_f_final=2.0 ** -14) for s in range(2)] + \
+                 [W._inst(R.POTTS, 8, 10, 4, 2, 300 + s, ln_f_final=2.0 ** -14) for s in range(2)]
+    gen = R.Rewl([R.instance(**d) for d in train_inst], stream=stream)
+    assert gen.run_to_convergence(1000, 3_000_000, poll_cycles=20)
+    X, T = WS.training_set(gen, train_inst)
+    net = R.Mlp(max_batch=4096, seed=11, stream=stream)
+    hist = WS.train(net, X, T, steps=1500, batch=4096, lr=2e-3, seed=2, log_every=500)
+    assert hist[-1][1] < 1e-4, hist
+
+    L, seeds = 16, 6
+    ex = _golden(L)
+    targets = [W._inst(R.ISING, L, 2, 4, 2, 500 + s) for s in range(seeds)]
+    results = {}
+    for mode in ("plain", "warm"):
+        ctx = R.Rewl([R.instance(**d) for d in targets], stream=stream)
+        if mode == "warm":
+            for k in range(seeds):
+                ctx.warm_start(k, net, 2.0 ** -4)
+        assert ctx.run_to_convergence(1000, 5_000_000, poll_cycles=10)
+        sweeps, eps = [], []
+        for k in range(seeds):
+            c = ctx.counters(k)
+            sweeps.append(int(c["conv_sweep"].max()))
+            lg, _ = ctx.get_dos(k)
+            eps.append(cc.mean_relative_error(lg, ex))
+        results[mode] = (np.array(sweeps), np.array(eps))
+    ps, pe = results["plain"]
+    ws, we = results["warm"]
+    print(f"plain sweeps {ps.mean():.0f} eps {pe.mean():.2e} | warm sweeps {ws.mean():.0f} eps {we.mean():.2e}")
+    assert ws.mean() < ps.mean()
+    assert we.mean() < 1.5 * pe.mean() + 2e-3

@@ -351,3 +351,28 @@ def test_concatenate_reassembles_exact_pieces():
     lg, joins = cc.concatenate(pieces, lo, w, reach, 4.0, math.log(2))
     assert np.allclose(lg[reach.astype(bool)], ex[reach.astype(bool)], atol=1e-9)
     assert np.all(np.diff(joins) > 0)
+
+
+# ---------------------------------------------------------------------------
+# warm-start network reference: chain-rule gradient against finite differences
+# ---------------------------------------------------------------------------
+def test_mlp_reference_gradient_matches_finite_differences():
+    from oracle import mlp as M
+    rng = np.random.default_rng(0)
+    p = M.init_params(1)
+    x = rng.normal(size=(7, 5))
+    t = rng.normal(size=7)
+    g = M.gradient(p, x, t)
+    idx = rng.choice(M.N_PARAMS, 60, replace=False)
+    idx = np.concatenate([idx, [0, 639, 640, 767, M.N_PARAMS - 129, M.N_PARAMS - 1]])
+    for i in idx:
+        h = 1e-6
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (M.loss(pp, x, t) - M.loss(pm, x, t)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(fd), (i, fd, g[i])
+    # one Adam step moves every parameter against its gradient
+    p2, m, v = M.adam_step(p, np.zeros_like(p), np.zeros_like(p), g, 1, 1e-3)
+    moved = np.sign(p - p2)[np.abs(g) > 1e-12]
+    assert np.all(moved == np.sign(g[np.abs(g) > 1e-12]))
