@@ -214,6 +214,21 @@ long rewl_mlp_launch_count(const rewl_mlp *net);
 const char *rewl_mlp_last_error(const rewl_mlp *net);
 void rewl_mlp_destroy(rewl_mlp *net);
 
+/* Forward pass that allocates nothing (the paper has no counterpart; this is
+ * a library service).  For callers that must not allocate device memory once
+ * running -- their device memory belongs to another allocator (a framework's
+ * caching pool, a budget fixed at start-up) or cudaMalloc's implicit
+ * synchronisation of the device is not acceptable where they call from.
+ * params: device pointer to the 33921 FP32 parameters (layout above); x: device
+ * [n][5]; y: device [n]; n a multiple of 64, at most 1024 (REWL_EINVAL
+ * otherwise, message in rewl_mlp_last_error(NULL)).  The activations live in a
+ * static device array of 3,276,800 bytes that every GPU loading the library
+ * holds until exit; the first call on a device looks up its address there (so
+ * make that first call before any stream capture).  All calls share the
+ * array: calls whose work overlaps on the GPU race.  Asynchronous on
+ * cuda_stream (NULL: the legacy default stream); calls no allocator. */
+rewl_status rewl_mlp_forward_noalloc(const float *params, const float *x, float *y, int n, void *cuda_stream);
+
 /* Warm start of instance `inst`: every walker of window i gets
  * ln g(E) = N s(E) (shifted so the window's smallest realisable value is 0,
  * rounded to 2^-32), H = 0, and ln f = ln_f_start (a power of two; 0 freezes). */

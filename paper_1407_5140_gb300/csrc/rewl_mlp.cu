@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -645,3 +646,94 @@ int mlp_warm_start(rewl_mlp *net, const DevState &st, int inst, int h, int w, in
 }
 
 }  // namespace rewl
+
+// ---------------------------------------------------------------------------
+// Forward pass without any allocation (rewl_mlp_forward_noalloc).
+//
+// Some callers cannot allocate device memory once they are running: their
+// device memory belongs to another allocator (a framework's caching pool or a
+// fixed budget fixed at start-up), or they call from a loop where cudaMalloc's
+// implicit synchronisation of the whole device is not acceptable.  For them
+// the activations of one forward pass live in this file-scope device array,
+// loaded with the library and held by every GPU that loads it until the
+// process exits.  All calls share it: two calls whose work overlaps on the GPU
+// (different streams, or different host threads) race on it.  No entry of it
+// needs to start at zero -- the pass writes every value before reading it --
+// and it keeps whatever the last call left there.
+// ---------------------------------------------------------------------------
+namespace rewl {
+
+static constexpr int kNoAllocMaxBatch = 1024;
+// layout: H1, H2, H3 (FP32, n x 128 each), then BF16 H1b, H1Tb, H2b, H2Tb,
+// H3b, H3Tb (n x 128 each), then BF16 W2b, W3b, W2Tb, W3Tb (128 x 128 each)
+static constexpr size_t kNoAllocF32 = 3ull * kNoAllocMaxBatch * kH;
+static constexpr size_t kNoAllocBf16 = 6ull * kNoAllocMaxBatch * kH + 4ull * kH * kH;
+static constexpr size_t kNoAllocBytes = kNoAllocF32 * 4 + kNoAllocBf16 * 2;   // 3,276,800 bytes
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+}  // namespace rewl
+
+extern "C" rewl_status rewl_mlp_forward_noalloc(const float *params, const float *x, float *y, int n,
+                                                void *cuda_stream)
+{
+    // device address of the scratch array, looked up once per device with that
+    // device current (the host-side name is only a stand-in for it)
+    static std::mutex mu;
+    static void *addr[64] = {nullptr};
+    if (!params || !x || !y) return mfail(nullptr, REWL_EINVAL, "rewl_mlp_forward_noalloc: null pointer");
+    if (n < 64 || n % 64 || n > kNoAllocMaxBatch)
+        return mfail(nullptr, REWL_EINVAL,
+                     "rewl_mlp_forward_noalloc: n must be a multiple of 64 in [64, 1024] (static scratch limit)");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return mfail(nullptr, REWL_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64) return mfail(nullptr, REWL_EINVAL, "rewl_mlp_forward_noalloc: device index above 63");
+    void *base;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!addr[dev]) {
+            e = cudaGetSymbolAddress(&addr[dev], g_noalloc_scratch);
+            if (e != cudaSuccess) {
+                addr[dev] = nullptr;
+                return mfail(nullptr, REWL_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            }
+        }
+        base = addr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t NB = (size_t)n * kH;
+    float *H1 = reinterpret_cast<float *>(base);
+    float *H2 = H1 + (size_t)kNoAllocMaxBatch * kH;
+    float *H3 = H2 + (size_t)kNoAllocMaxBatch * kH;
+    bf16 *b0 = reinterpret_cast<bf16 *>(reinterpret_cast<unsigned char *>(base) + kNoAllocF32 * 4);
+    bf16 *H1b = b0, *H1Tb = b0 + NB, *H2b = b0 + 2 * NB, *H2Tb = b0 + 3 * NB, *H3b = b0 + 4 * NB,
+         *H3Tb = b0 + 5 * NB;
+    bf16 *W2b = b0 + 6ull * kNoAllocMaxBatch * kH, *W3b = W2b + kH * kH, *W2Tb = W3b + kH * kH,
+         *W3Tb = W2Tb + kH * kH;
+    cast_weights_kernel<<<(kH * kH + 255) / 256, 256, 0, s>>>(params, W2b, W3b, W2Tb, W3Tb);
+    layer1_kernel<<<(n * kH + 255) / 256, 256, 0, s>>>(x, params, n, H1, H1b, H1Tb);
+    GemmArgs a{};
+    a.A = H1b;
+    a.Bn = W2b;
+    a.M = n;
+    a.N = kH;
+    a.K = kH;
+    a.k_chunk = kH;
+    a.bias = params + kOffB2;
+    a.out_f = H2;
+    a.out_b = H2b;
+    a.out_bt = H2Tb;
+    gemm_kernel<kEpiForward><<<dim3(n / 64, kH / 64, 1), 128, 0, s>>>(a);
+    a.A = H2b;
+    a.Bn = W3b;
+    a.bias = params + kOffB3;
+    a.out_f = H3;
+    a.out_b = H3b;
+    a.out_bt = H3Tb;
+    gemm_kernel<kEpiForward><<<dim3(n / 64, kH / 64, 1), 128, 0, s>>>(a);
+    output_kernel<<<(n + 127) / 128, 128, 0, s>>>(H3, params, n, y, nullptr, nullptr, nullptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return mfail(nullptr, REWL_ECUDA, std::string("rewl_mlp_forward_noalloc: ") + cudaGetErrorString(e));
+    return REWL_OK;
+}

@@ -79,6 +79,7 @@ def lib():
         L.rewl_mlp_destroy.argtypes = [vp]
         L.rewl_mlp_destroy.restype = None
         L.rewl_warm_start.argtypes = [vp, i32, vp, f64]
+        L.rewl_mlp_forward_noalloc.argtypes = [vp, vp, vp, i32, vp]
         L.rewl_debug_lam.argtypes = [vp, vp, i64]
         L.rewl_debug_philox.argtypes = [u32, u32, vp, vp, i64]
         for name in ("rewl_create", "rewl_create_batch", "rewl_run", "rewl_exchange", "rewl_run_cycles",
@@ -86,7 +87,7 @@ def lib():
                      "rewl_geometry", "rewl_get_state", "rewl_get_counters", "rewl_set_option", "rewl_save",
                      "rewl_load", "rewl_debug_lam", "rewl_debug_philox", "rewl_mlp_create", "rewl_mlp_set_params",
                      "rewl_mlp_get_params", "rewl_mlp_forward", "rewl_mlp_gradient", "rewl_mlp_train_step",
-                     "rewl_warm_start"):
+                     "rewl_warm_start", "rewl_mlp_forward_noalloc"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -349,3 +350,12 @@ class Mlp:
 
     def launch_count(self):
         return int(lib().rewl_mlp_launch_count(self._h))
+
+
+def mlp_forward_noalloc(params, x, y, stream=None):
+    """rewl_mlp_forward_noalloc: network output without any device allocation.
+    params (33921 floats), x ([n, 5]) and y ([n]) are float32 CUDA tensors."""
+    code = lib().rewl_mlp_forward_noalloc(C.c_void_p(params.data_ptr()), C.c_void_p(x.data_ptr()),
+                                          C.c_void_p(y.data_ptr()), x.shape[0], _stream_ptr(stream))
+    if code != 0:
+        raise RewlError(code, lib().rewl_mlp_last_error(None).decode())
