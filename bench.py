@@ -146,6 +146,24 @@ def cpu_oracle_rate(ds, budget_s, threads):
     return done / total_t, desc, total_t
 
 
+def rank_instances(ds, rank):
+    """Weak scaling: every rank runs the whole batch with its own seeds."""
+    out = [dict(d) for d in ds]
+    for d in out:
+        d["seed"] += 1000 * rank
+    return out
+
+
+def max_over_ranks(value, world, device="cpu"):
+    """The slowest rank's step time (torch.distributed, any backend)."""
+    if world <= 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -154,9 +172,7 @@ def run_ours(args, rank, world):
 
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
-    ds = W.config1()
-    for d in ds:                       # weak scaling: each rank its own seeds
-        d["seed"] += 1000 * rank
+    ds = rank_instances(W.config1(), rank)
     attempts_per_step = W.attempts_per_sweep(ds) * SWEEPS_PER_STEP
     # a stream of our own: torch's default stream has handle 0, which the
     # library would replace by a stream it creates
@@ -182,11 +198,7 @@ def run_ours(args, rank, world):
             times.append(a.elapsed_time(b) / 1000.0)
         torch.cuda.synchronize()
     launches = ctx.launch_count() - launches0
-    t_step = sum(times) / len(times)
-    if world > 1:
-        tt = torch.tensor([t_step], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(sum(times) / len(times), world, device="cuda")
     value = attempts_per_step * world / t_step
     clocks = clk.summary()
 

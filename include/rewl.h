@@ -160,9 +160,12 @@ rewl_status rewl_get_counters(rewl_ctx *ctx, int inst, uint64_t *ex_prop, uint64
  * block (0 = auto, 1..4).  REWL_OPT_WINDOWS_PER_CTA: force windows per thread
  * block (0 = auto; at most 32 walkers per block).
  * REWL_OPT_MAX_SWEEPS_PER_LAUNCH: split long rewl_run calls (>= 1).
+ * REWL_OPT_AUTOTUNE: 1 (default) = before the first run, time a few launch
+ * shapes on a shadow copy of the batch (same descriptors, its own memory) and
+ * keep the fastest; 0 = shape rule only.  Shapes never change results.
  * Launch-shape options may only be set before the first run. */
 enum { REWL_OPT_CHECK_EVERY = 1, REWL_OPT_PRODUCER_WARPS = 2, REWL_OPT_WINDOWS_PER_CTA = 3,
-       REWL_OPT_MAX_SWEEPS_PER_LAUNCH = 4 };
+       REWL_OPT_MAX_SWEEPS_PER_LAUNCH = 4, REWL_OPT_AUTOTUNE = 5 };
 rewl_status rewl_set_option(rewl_ctx *ctx, int option, long value);
 
 /* Number of kernel launches this context enqueued so far (graph replays count

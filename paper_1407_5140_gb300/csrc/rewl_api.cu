@@ -67,6 +67,8 @@ struct rewl_ctx {
     long check_every = 1;
     long max_sweeps_per_launch = 1L << 30;
     int force_producers = 0, force_wpc = 0;
+    int tune_mode = 1;                  // 1: measure candidate shapes, 0: rule only
+    int tune_target = 0, tune_bias = 0; // chosen walkers-per-block target / producer bias
     bool planned = false;
     cudaGraphExec_t graph = nullptr;
     long graph_sweeps = -1;
@@ -408,10 +410,59 @@ void rewl::class_shape(const rewl_ctx *ctx, int ci, int *model, int *N, int *w, 
 int rewl::total_walkers(const rewl_ctx *ctx) { return ctx->n_slots; }
 int rewl::forced_producers(const rewl_ctx *ctx) { return ctx->force_producers; }
 int rewl::forced_wpc(const rewl_ctx *ctx) { return ctx->force_wpc; }
+int rewl::tune_target(const rewl_ctx *ctx) { return ctx->tune_target; }
+int rewl::tune_producer_bias(const rewl_ctx *ctx) { return ctx->tune_bias; }
+
+// Time a few launch shapes on a shadow context built from the same
+// descriptors (its own memory and stream; the caller's walkers are not
+// touched) and keep the fastest.  Results do not depend on the shape.
+static void measure_shapes(rewl_ctx *ctx)
+{
+    if (ctx->tune_mode != 1 || ctx->force_wpc || ctx->force_producers) return;
+    std::vector<rewl_instance> desc;
+    long long trials = 0;
+    for (auto &h : ctx->inst) {
+        desc.push_back(h.desc);
+        trials += (long long)h.dev.h * h.dev.m * h.dev.N;
+    }
+    const long sweeps = std::max(3L, std::min(50L, (long)(40000000LL / std::max(1LL, trials))));
+    const int targets[] = {4, 8, 16, 32};
+    const int biases[] = {0, 1};
+    float best = 0.f;
+    for (int t : targets)
+        for (int b : biases) {
+            rewl_ctx *sh = nullptr;
+            if (rewl_create_batch(&sh, desc.data(), (int)desc.size(), nullptr) != REWL_OK) {
+                rewl_destroy(sh);
+                return;
+            }
+            sh->tune_mode = 0;
+            sh->tune_target = t;
+            sh->tune_bias = b;
+            sh->check_every = ctx->check_every;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            float ms = -1.f;
+            if (rewl_run(sh, 1) == REWL_OK && cudaEventCreate(&e0) == cudaSuccess &&
+                cudaEventCreate(&e1) == cudaSuccess && cudaEventRecord(e0, sh->stream) == cudaSuccess &&
+                rewl_run(sh, sweeps) == REWL_OK && cudaEventRecord(e1, sh->stream) == cudaSuccess &&
+                cudaEventSynchronize(e1) == cudaSuccess)
+                cudaEventElapsedTime(&ms, e0, e1);
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            rewl_destroy(sh);
+            if (ms > 0.f && (best == 0.f || ms < best)) {
+                best = ms;
+                ctx->tune_target = t;
+                ctx->tune_bias = b;
+            }
+        }
+    cudaGetLastError();
+}
 
 static rewl_status plan(rewl_ctx *ctx)
 {
     if (ctx->planned) return REWL_OK;
+    measure_shapes(ctx);
     std::map<std::vector<int>, int> key2c;
     for (int k = 0; k < (int)ctx->inst.size(); ++k) {
         const InstDev &I = ctx->inst[k].dev;
@@ -867,6 +918,11 @@ extern "C" rewl_status rewl_set_option(rewl_ctx *ctx, int option, long value)
             if (value < 0) return fail(ctx, REWL_EINVAL, "windows per block must be >= 0");
             if (ctx->planned) return fail(ctx, REWL_ESTATE, "launch plan already fixed");
             ctx->force_wpc = (int)value;
+            break;
+        case REWL_OPT_AUTOTUNE:
+            if (value != 0 && value != 1) return fail(ctx, REWL_EINVAL, "autotune must be 0 (rule) or 1 (measure)");
+            if (ctx->planned) return fail(ctx, REWL_ESTATE, "launch plan already fixed");
+            ctx->tune_mode = (int)value;
             break;
         case REWL_OPT_MAX_SWEEPS_PER_LAUNCH:
             if (value < 1) return fail(ctx, REWL_EINVAL, "max sweeps per launch must be >= 1");

@@ -132,4 +132,6 @@ void class_shape(const rewl_ctx *ctx, int c, int *model, int *N, int *w, int *m,
 int total_walkers(const rewl_ctx *ctx);
 int forced_producers(const rewl_ctx *ctx);
 int forced_wpc(const rewl_ctx *ctx);
+int tune_target(const rewl_ctx *ctx);          // walkers-per-block target (0: rule)
+int tune_producer_bias(const rewl_ctx *ctx);   // added to the rule's producer warps
 }  // namespace rewl

@@ -1,8 +1,11 @@
 // rewl_tune.cu -- launch-shape choice for the sweep kernel: windows per thread
 // block (walkers per consumer warp) and producer warps per block, per size
-// class.  Never changes results: every random number is keyed by (instance,
-// window, walker, draw index), walkers of one window always share a block, and
-// each walker's trials are resolved in draw order by one consumer lane.
+// class.  A rule maps (walkers-per-block target, producer bias) to a shape;
+// the host library measures a few targets and biases on a shadow copy of the
+// batch and keeps the fastest (rewl_api.cu: measure_shapes).  Never changes
+// results: every random number is keyed by (instance, window, walker, draw
+// index), walkers of one window always share a block, and each walker's
+// trials are resolved in draw order by one consumer lane.
 #include <algorithm>
 
 #include "rewl_internal.h"
@@ -37,6 +40,7 @@ int autotune_plan(rewl_ctx *ctx)
 {
     const int nc = class_count(ctx);
     const int tot = total_walkers(ctx);
+    const int target = tune_target(ctx), bias = tune_producer_bias(ctx);
     for (int c = 0; c < nc; ++c) {
         int model, N, w, m, lw;
         class_shape(ctx, c, &model, &N, &w, &m, &lw);
@@ -44,11 +48,12 @@ int autotune_plan(rewl_ctx *ctx)
         if (sweep_smem_bytes(m, 1, w, lw) > 227 * 1024) return 1;
         int wpc = forced_wpc(ctx);
         if (!wpc) {
-            wpc = std::max(1, pick_walkers(tot) / m);
+            wpc = std::max(1, (target ? target : pick_walkers(tot)) / m);
             while (wpc > 1 && (wpc * m > 32 || sweep_smem_bytes(wpc * m, wpc, w, lw) > kSmemBudget)) --wpc;
         }
         if (wpc * m > 32 || sweep_smem_bytes(wpc * m, wpc, w, lw) > 227 * 1024) return 1;
-        const int prod = forced_producers(ctx) ? forced_producers(ctx) : pick_producers(model, wpc * m);
+        const int prod = forced_producers(ctx) ? forced_producers(ctx)
+                                               : std::max(1, std::min(4, pick_producers(model, wpc * m) + bias));
         plan_class(ctx, c, wpc, prod);
     }
     return 0;

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "librewl.so")
 
 ISING, POTTS = 0, 1
-OPT_CHECK_EVERY, OPT_PRODUCER_WARPS, OPT_WINDOWS_PER_CTA, OPT_MAX_SWEEPS_PER_LAUNCH = 1, 2, 3, 4
+OPT_CHECK_EVERY, OPT_PRODUCER_WARPS, OPT_WINDOWS_PER_CTA, OPT_MAX_SWEEPS_PER_LAUNCH, OPT_AUTOTUNE = 1, 2, 3, 4, 5
 STATUS = {0: "REWL_OK", -1: "REWL_EINVAL", -2: "REWL_ENOMEM", -3: "REWL_ECUDA", -4: "REWL_ETIMEOUT",
           -5: "REWL_ESTATE", -6: "REWL_EDEVICE"}
 

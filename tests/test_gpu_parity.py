@@ -228,3 +228,56 @@ def _golden_lng(L, B):
     for E, lg in rows:
         out[(int(E) + 2 * N) // 4] = lg
     return out
+
+
+def test_config3_uneven_batch_sampled_instances_match_oracle():
+    # the uneven-size batch (96 instances of mixed model and L) in one context;
+    # one instance of each (model, L) re-run on the oracle
+    ds = W.config3()
+    gpu = make_gpu(ds)
+    gpu.run(3)
+    gpu.exchange()
+    gpu.run(2)
+    seen = {}
+    for k, d in enumerate(ds):
+        seen.setdefault((d["model"], d["L"]), k)
+    for (model, L), k in sorted(seen.items()):
+        o = make_oracle(ds[k])
+        o.init()
+        o.run(3)
+        o.exchange()
+        o.run(2)
+        assert_same_state(gpu, k, o, f"config3 instance {k} (model {model}, L {L})")
+
+
+def test_potts_q10_full_convergence_invariants():
+    # q = 10 Potts: sum_E g(E) = q^N checked in log space, and the full
+    # converged run agrees with the oracle bit for bit at L = 8
+    d = _potts(8, 10, 4, 2, seed=4)
+    gpu = make_gpu([d])
+    orc = make_oracle(d)
+    orc.init()
+    for c in range(400):
+        step_both(gpu, [orc], 1000)
+        if orc.all_converged():
+            break
+    assert orc.all_converged() and gpu.status(0)["all_converged"]
+    assert_same_state(gpu, 0, orc, "potts q10 L8 converged")
+    lg, _ = gpu.get_dos(0)
+    from oracle.exact_dos import log_sum
+    N = 64
+    assert abs(log_sum(lg) - N * math.log(10)) < 2e-3 * N * math.log(10)
+
+
+def test_potts_q10_l32_config2_log_sum_invariant():
+    # the q = 10, L = 32 workload (32 windows x 8 walkers) run to ln f = 2^-20:
+    # ln sum_E g(E) must be 1024 ln 10
+    ds = W.config2()
+    gpu = make_gpu(ds)
+    assert gpu.run_to_convergence(1000, 3_000_000, poll_cycles=50)
+    lg, _ = gpu.get_dos(0)
+    from oracle.exact_dos import log_sum
+    target = 1024 * math.log(10)
+    assert abs(log_sum(lg) - target) < 2e-3 * target, (log_sum(lg), target)
+    c = gpu.counters(0)
+    assert np.all(c["ex_acc"][:31] > 0)
