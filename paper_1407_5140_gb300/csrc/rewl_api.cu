@@ -52,7 +52,7 @@ struct rewl_ctx {
     int32_t *d_cfg = nullptr, *d_E = nullptr, *d_bin = nullptr, *d_replica = nullptr, *d_slot_inst = nullptr;
     ull *d_draw = nullptr, *d_nacc = nullptr;
     uint8_t *d_latch = nullptr;
-    long long *d_lng = nullptr;
+    long long *d_lng = nullptr, *d_lng0 = nullptr;
     uint32_t *d_H = nullptr, *d_lat = nullptr;
     uint8_t *d_reach = nullptr;
     ull *d_counters = nullptr;
@@ -267,6 +267,7 @@ extern "C" rewl_status rewl_create_batch(rewl_ctx **out, const rewl_instance *in
     CK(dalloc(&ctx->d_nacc, slot));
     CK(dalloc(&ctx->d_latch, slot));
     CK(dalloc(&ctx->d_lng, lng));
+    CK(dalloc(&ctx->d_lng0, lng));
     CK(dalloc(&ctx->d_H, lng));
     CK(dalloc(&ctx->d_lat, lat));
     CK(dalloc(&ctx->d_reach, rch));
@@ -288,6 +289,7 @@ extern "C" rewl_status rewl_create_batch(rewl_ctx **out, const rewl_instance *in
     CK(cudaMemsetAsync(ctx->d_ex_prop, 0, 8 * win, s));
     CK(cudaMemsetAsync(ctx->d_ex_acc, 0, 8 * win, s));
     CK(cudaMemsetAsync(ctx->d_lng, 0, 8 * lng, s));
+    CK(cudaMemsetAsync(ctx->d_lng0, 0, 8 * lng, s));
     CK(cudaMemsetAsync(ctx->d_H, 0, 4 * lng, s));
     CK(cudaMemsetAsync(ctx->d_counters, 0, 16, s));
     CK(cudaMemsetAsync(ctx->d_error, 0, 4, s));
@@ -308,6 +310,7 @@ extern "C" rewl_status rewl_create_batch(rewl_ctx **out, const rewl_instance *in
     st.n_acc = ctx->d_nacc;
     st.replica = ctx->d_replica;
     st.lng = ctx->d_lng;
+    st.lng0 = ctx->d_lng0;
     st.H = ctx->d_H;
     st.lat = ctx->d_lat;
     st.reach = ctx->d_reach;
@@ -357,7 +360,7 @@ extern "C" void rewl_destroy(rewl_ctx *ctx)
     }
     void *bufs[] = {ctx->d_inst, ctx->d_lo, ctx->d_nreach, ctx->d_stage, ctx->d_conv, ctx->d_conv_sweep,
                     ctx->d_ex_prop, ctx->d_ex_acc, ctx->d_cfg, ctx->d_E, ctx->d_bin, ctx->d_replica,
-                    ctx->d_slot_inst, ctx->d_draw, ctx->d_nacc, ctx->d_latch, ctx->d_lng, ctx->d_H,
+                    ctx->d_slot_inst, ctx->d_draw, ctx->d_nacc, ctx->d_latch, ctx->d_lng, ctx->d_lng0, ctx->d_H,
                     ctx->d_lat, ctx->d_reach, ctx->d_counters, ctx->d_error, ctx->d_ex0, ctx->d_ex1};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -709,7 +712,26 @@ extern "C" rewl_status rewl_get_state(rewl_ctx *ctx, int inst, int8_t *spins, in
         CK(dget(u, ctx->d_lng + I.lng_off, (size_t)nw * I.w));
         for (size_t i = 0; i < u.size(); ++i) ln_g[i] = std::ldexp((double)u[i], -32);
     }
-    if (H) CK(cudaMemcpy(H, ctx->d_H + I.lng_off, 4 * (size_t)nw * I.w, cudaMemcpyDeviceToHost));
+    if (H) {
+        // converged windows count H; elsewhere H = (ln g - ln g at the stage
+        // start) / ln f, exact in 2^-32 units with ln f = 2^(32 - stage)
+        std::vector<long long> u, u0;
+        std::vector<int32_t> sg;
+        std::vector<uint8_t> cv;
+        CK(dget(u, ctx->d_lng + I.lng_off, (size_t)nw * I.w));
+        CK(dget(u0, ctx->d_lng0 + I.lng_off, (size_t)nw * I.w));
+        CK(dget(sg, ctx->d_stage + I.win0, I.h));
+        CK(dget(cv, ctx->d_conv + I.win0, I.h));
+        CK(cudaMemcpy(H, ctx->d_H + I.lng_off, 4 * (size_t)nw * I.w, cudaMemcpyDeviceToHost));
+        for (int k = 0; k < nw; ++k) {
+            const int win = k / I.m;
+            if (cv[win]) continue;
+            for (int bb = 0; bb < I.w; ++bb) {
+                const size_t i = (size_t)k * I.w + bb;
+                H[i] = (uint32_t)((u[i] - u0[i]) >> (32 - sg[win]));
+            }
+        }
+    }
     if (stage) CK(cudaMemcpy(stage, ctx->d_stage + I.win0, 4 * I.h, cudaMemcpyDeviceToHost));
     if (conv) CK(cudaMemcpy(conv, ctx->d_conv + I.win0, I.h, cudaMemcpyDeviceToHost));
     if (latch) CK(cudaMemcpy(latch, ctx->d_latch + I.slot0, nw, cudaMemcpyDeviceToHost));
@@ -872,6 +894,7 @@ extern "C" rewl_status rewl_set_initial_lng(rewl_ctx *ctx, int inst, const doubl
             for (int j = 0; j < I.m; ++j) u[((size_t)i * I.m + j) * I.w + b] = (long long)units;
         }
     CK(cudaMemcpy(ctx->d_lng + I.lng_off, u.data(), 8 * u.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_lng0 + I.lng_off, u.data(), 8 * u.size(), cudaMemcpyHostToDevice));
     CK(cudaMemset(ctx->d_H + I.lng_off, 0, 4 * u.size()));
     CK(cudaMemset(ctx->d_latch + I.slot0, 0, (size_t)I.h * I.m));
     std::vector<int32_t> st(I.h, k0 < 0 ? 0 : k0);
@@ -950,7 +973,7 @@ extern "C" const char *rewl_last_error(const rewl_ctx *ctx)
 // ---------------------------------------------------------------------------
 // checkpoint
 // ---------------------------------------------------------------------------
-static const char kMagic[8] = {'R', 'E', 'W', 'L', 'C', 'K', 'P', '1'};
+static const char kMagic[8] = {'R', 'E', 'W', 'L', 'C', 'K', 'P', '2'};
 
 template <class T>
 static bool wr(FILE *f, const std::vector<T> &v)
@@ -981,6 +1004,7 @@ static bool rd(FILE *f, std::vector<T> &v)
     X(ull, d_nacc, ctx->n_slots)                      \
     X(uint8_t, d_latch, ctx->n_slots)                 \
     X(long long, d_lng, (size_t)ctx->n_lng)           \
+    X(long long, d_lng0, (size_t)ctx->n_lng)          \
     X(uint32_t, d_H, (size_t)ctx->n_lng)              \
     X(uint32_t, d_lat, (size_t)ctx->n_lat)            \
     X(ull, d_counters, 2)

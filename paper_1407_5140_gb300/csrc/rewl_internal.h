@@ -74,6 +74,11 @@ struct DevState {
     int32_t *replica;
     // per walker, per bin
     long long *lng;
+    // ln g when the window's current stage began.  Every trial adds ln f to
+    // ln g of the bin it ends in, so while ln f > 0 the stage's histogram is
+    // H = (ln g - lng0) / ln f exactly; H below counts visits only in
+    // converged windows (ln f = 0) and stays 0 elsewhere.
+    long long *lng0;
     uint32_t *H;
     // configurations
     uint32_t *lat;

@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "rewl_device.cuh"
 #include "rewl_internal.h"
@@ -291,12 +292,13 @@ __device__ __forceinline__ void st_shared_s64_if(bool p, uint32_t addr, long lon
                  : "memory");
 }
 
-__device__ __forceinline__ void red_add_global_u32_if(bool p, uint32_t *ptr)
+__device__ __forceinline__ void red_add_global_u32_if(bool p, uint32_t *ptr, uint32_t v)
 {
-    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q red.relaxed.gpu.global.add.u32 [%1], 1;\n}" ::"r"(
+    // no "memory" clobber: H is read only after a block-wide barrier, and
+    // shared-memory loads stay free to move across the reduction
+    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q red.relaxed.gpu.global.add.u32 [%1], %2;\n}" ::"r"(
                      (uint32_t)p),
-                 "l"(ptr)
-                 : "memory");
+                 "l"(ptr), "r"(v));
 }
 
 __device__ __forceinline__ void named_sync(int id, int nthreads)
@@ -319,7 +321,9 @@ enum : int { kBarFull = 1, kBarEmpty = 3 };  // ids 1, 2 (full) and 3, 4 (empty)
 // consumer keeps the trial chain short: the next trial's lattice values are
 // read one trial ahead and its bin change is computed for both outcomes of
 // the current trial; ln g of the reachable bins is read before the bin change
-// is known; H is counted in global memory with fire-and-forget reductions.
+// is known.  H needs no per-trial work while ln f > 0 (it is read off ln g
+// and its value at the stage start); converged windows count it in global
+// memory with fire-and-forget reductions.
 template <int MODEL>
 __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkItem *items, SweepArgs args)
 {
@@ -353,6 +357,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
 
     const int slot_base = I.slot0 + it.win_begin * m;
     uint32_t *Hblk = st.H + I.lng_off + (long long)it.win_begin * m * w;   // this block's histograms
+    long long *lng0blk = st.lng0 + I.lng_off + (long long)it.win_begin * m * w;
     // ---- load state into shared memory
     for (int i = tid; i < nw * wg; i += nthreads) {
         const int k = i / wg, bb = i - k * wg - kGuard;
@@ -443,87 +448,102 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
             const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
             // shared address of ln g of global bin 0 of this walker (bins lo..hi valid)
             const uint32_t lng_sa = (uint32_t)__cvta_generic_to_shared(lng_s + (size_t)tv * wg + kGuard) - 8u * (uint32_t)lo;
-            for (int k = 0; k < rounds; ++k) {
-                const int slot = k & 1;
-                named_sync(kBarFull + slot, nthreads);
-                const int cnt = min(kR, N - k * kR);
-                const Trial *rr = ring + (size_t)slot * kR * nw + tv;   // record a at rr[a * nw]
-                Trial t = rr[0];
-                Trial t1 = rr[cnt > 1 ? nw : 0];
-                const Nbr n0 = load_nbr<MODEL>(smem, t);
-                int db = bin_change<MODEL>(n0, t, q);     // bin change of the current trial
-                uint32_t sv = n0.s;                        // its site word (Ising) / value (Potts)
-                bool acc_prev = false;
-#pragma unroll 3
-                for (int a = 0; a < cnt; ++a) {
-                    const Trial t2 = rr[(size_t)(a + 2 < cnt ? a + 2 : cnt - 1) * nw];
-                    // the next trial's lattice values, read before this trial's move
-                    const Nbr nn = load_nbr<MODEL>(smem, t1);
-                    // ln g of every bin a move can reach, before the move is known
-                    const long long sm1 = lng[b - 1], sp1 = lng[b + 1], sm2 = lng[b - 2], sp2 = lng[b + 2];
-                    long long sm3 = 0, sp3 = 0, sm4 = 0, sp4 = 0;
-                    if (MODEL == kPotts) {
-                        sm3 = lng[b - 3];
-                        sp3 = lng[b + 3];
-                        sm4 = lng[b - 4];
-                        sp4 = lng[b + 4];
+            // the rounds of one sweep; kCountH adds the H counting of
+            // converged windows, compiled out where the warp has none: a run
+            // of trials that end in the same bin is added to H when the walker
+            // leaves the bin (and at the end of the sweep)
+            uint32_t run = 0;
+            auto sweep_rounds = [&](auto count_h) {
+                constexpr bool kCountH = decltype(count_h)::value;
+                for (int k = 0; k < rounds; ++k) {
+                    const int slot = k & 1;
+                    named_sync(kBarFull + slot, nthreads);
+                    const int cnt = min(kR, N - k * kR);
+                    const Trial *rr = ring + (size_t)slot * kR * nw + tv;   // record a at rr[a * nw]
+                    Trial t = rr[0];
+                    Trial t1 = rr[cnt > 1 ? nw : 0];
+                    const Nbr n0 = load_nbr<MODEL>(smem, t);
+                    int db = bin_change<MODEL>(n0, t, q);     // bin change of the current trial
+                    uint32_t sv = n0.s;                        // its site word (Ising) / value (Potts)
+                    bool acc_prev = false;
+    #pragma unroll 3
+                    for (int a = 0; a < cnt; ++a) {
+                        const Trial t2 = rr[(size_t)(a + 2 < cnt ? a + 2 : cnt - 1) * nw];
+                        // the next trial's lattice values, read before this trial's move
+                        const Nbr nn = load_nbr<MODEL>(smem, t1);
+                        // ln g of every bin a move can reach, before the move is known
+                        const long long sm1 = lng[b - 1], sp1 = lng[b + 1], sm2 = lng[b - 2], sp2 = lng[b + 2];
+                        long long sm3 = 0, sp3 = 0, sm4 = 0, sp4 = 0;
+                        if (MODEL == kPotts) {
+                            sm3 = lng[b - 3];
+                            sp3 = lng[b + 3];
+                            sm4 = lng[b - 4];
+                            sp4 = lng[b + 4];
+                        }
+                        // rare: the previous trial moved this trial's site or a
+                        // neighbour after db and sv were taken -- read them again
+                        if (acc_prev && (t.aux & kNear)) {
+                            const Nbr nf = load_nbr<MODEL>(smem, t);
+                            db = bin_change<MODEL>(nf, t, q);
+                            sv = nf.s;
+                        }
+                        // this trial's move: Ising flips one bit of the site word,
+                        // Potts writes the new value
+                        uint32_t moved;
+                        if (MODEL == kIsing) {
+                            moved = sv ^ t.mx;
+                        } else {
+                            int nv = (int)sv + (int)(t.aux & 0xFFFFu);
+                            nv -= nv >= q ? q : 0;
+                            moved = (uint32_t)nv;
+                        }
+                        // accept iff ln g(E') < ln g(E) + lam, i.e. with min(1, g(E)/g(E'))
+                        const int bn = b + db;
+                        const bool inw = (unsigned)(bn - lo) < (unsigned)w;
+                        const long long thr = cur + t.lam;
+                        long long v;
+                        if (MODEL == kIsing) {
+                            const long long p1 = db < 0 ? sm1 : sp1, p2 = db < 0 ? sm2 : sp2;
+                            v = (db & 1) ? p1 : p2;
+                        } else {
+                            const int ad = db < 0 ? -db : db;
+                            const long long p1 = db < 0 ? sm1 : sp1, p2 = db < 0 ? sm2 : sp2;
+                            const long long p3 = db < 0 ? sm3 : sp3, p4 = db < 0 ? sm4 : sp4;
+                            const long long p12 = (ad & 1) ? p1 : p2, p34 = (ad & 1) ? p3 : p4;
+                            v = ad > 2 ? p34 : p12;
+                        }
+                        v = db == 0 ? cur : v;
+                        const bool acc = inw && (v < thr);
+                        if (MODEL == kIsing) st_shared_u32_if(valid && acc, sbase + t.a_s, moved);
+                        else st_shared_u8_if(valid && acc, sbase + t.a_s, moved);
+                        // the next trial's bin change and site word from the values
+                        // read before this move (the flag above catches the cases
+                        // where this move changes them; an Ising site word shared
+                        // with this trial's site gets the flipped bit here)
+                        const int db_next = bin_change<MODEL>(nn, t1, q);
+                        uint32_t sv_next = nn.s;
+                        if (MODEL == kIsing) sv_next ^= (acc && t1.a_s == t.a_s) ? t.mx : 0u;
+                        if (kCountH) {
+                            const bool leave = acc && db != 0;
+                            red_add_global_u32_if(valid && frozen && leave, H + b, run);
+                            run = leave ? 1u : run + 1u;
+                        }
+                        b = acc ? bn : b;
+                        cur = (acc ? v : cur) + lnf;
+                        acc_count += acc ? 1u : 0u;
+                        st_shared_s64_if(valid, lng_sa + 8u * (uint32_t)b, cur);
+                        acc_prev = acc;
+                        db = db_next;
+                        sv = sv_next;
+                        t = t1;
+                        t1 = t2;
                     }
-                    // rare: the previous trial moved this trial's site or a
-                    // neighbour after db and sv were taken -- read them again
-                    if (acc_prev && (t.aux & kNear)) {
-                        const Nbr nf = load_nbr<MODEL>(smem, t);
-                        db = bin_change<MODEL>(nf, t, q);
-                        sv = nf.s;
-                    }
-                    // this trial's move: Ising flips one bit of the site word,
-                    // Potts writes the new value
-                    uint32_t moved;
-                    if (MODEL == kIsing) {
-                        moved = sv ^ t.mx;
-                    } else {
-                        int nv = (int)sv + (int)(t.aux & 0xFFFFu);
-                        nv -= nv >= q ? q : 0;
-                        moved = (uint32_t)nv;
-                    }
-                    // accept iff ln g(E') < ln g(E) + lam, i.e. with min(1, g(E)/g(E'))
-                    const int bn = b + db;
-                    const bool inw = (unsigned)(bn - lo) < (unsigned)w;
-                    const long long thr = cur + t.lam;
-                    long long v;
-                    if (MODEL == kIsing) {
-                        const long long p1 = db < 0 ? sm1 : sp1, p2 = db < 0 ? sm2 : sp2;
-                        v = (db & 1) ? p1 : p2;
-                    } else {
-                        const int ad = db < 0 ? -db : db;
-                        const long long p1 = db < 0 ? sm1 : sp1, p2 = db < 0 ? sm2 : sp2;
-                        const long long p3 = db < 0 ? sm3 : sp3, p4 = db < 0 ? sm4 : sp4;
-                        const long long p12 = (ad & 1) ? p1 : p2, p34 = (ad & 1) ? p3 : p4;
-                        v = ad > 2 ? p34 : p12;
-                    }
-                    v = db == 0 ? cur : v;
-                    const bool acc = inw && (v < thr);
-                    if (MODEL == kIsing) st_shared_u32_if(valid && acc, sbase + t.a_s, moved);
-                    else st_shared_u8_if(valid && acc, sbase + t.a_s, moved);
-                    // the next trial's bin change and site word from the values
-                    // read before this move (the flag above catches the cases
-                    // where this move changes them; an Ising site word shared
-                    // with this trial's site gets the flipped bit here)
-                    const int db_next = bin_change<MODEL>(nn, t1, q);
-                    uint32_t sv_next = nn.s;
-                    if (MODEL == kIsing) sv_next ^= (acc && t1.a_s == t.a_s) ? t.mx : 0u;
-                    b = acc ? bn : b;
-                    cur = (acc ? v : cur) + lnf;
-                    acc_count += acc ? 1u : 0u;
-                    st_shared_s64_if(valid, lng_sa + 8u * (uint32_t)b, cur);
-                    red_add_global_u32_if(valid, H + b);
-                    acc_prev = acc;
-                    db = db_next;
-                    sv = sv_next;
-                    t = t1;
-                    t1 = t2;
+                    if (k + 2 < rounds) named_arrive(kBarEmpty + slot, nthreads);
                 }
-                if (k + 2 < rounds) named_arrive(kBarEmpty + slot, nthreads);
-            }
+            };
+            if (__any_sync(0xffffffffu, valid && frozen)) sweep_rounds(std::true_type{});
+            else sweep_rounds(std::false_type{});
+            red_add_global_u32_if(valid && frozen && run != 0u, H + b, run);
             n_acc += acc_count;
         }
         __syncthreads();
@@ -535,7 +555,8 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
             for (int wk = warp; wk < nw; wk += nthreads / 32) {
                 const int wlk = wk / m;
                 const long long *lk = lng_s + (size_t)wk * wg + kGuard;
-                const uint32_t *hk = Hblk + (size_t)wk * w;
+                const long long *l0 = lng0blk + (size_t)wk * w;
+                const int shift = 32 - wstage_s[wlk];   // ln f = 2^(32 - stage) units
                 unsigned long long mn = ~0ull, sum = 0ull;
                 long long amax = 0;
                 for (int bb = lane; bb < w; bb += 32) {
@@ -543,7 +564,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                     const long long av = v < 0 ? -v : v;
                     amax = av > amax ? av : amax;
                     if (reach_s[wlk * w + bb]) {
-                        const unsigned long long hv = __ldcg(hk + bb);
+                        const unsigned long long hv = (unsigned long long)((v - __ldcg(l0 + bb)) >> shift);
                         mn = hv < mn ? hv : mn;
                         sum += hv;
                     }
@@ -572,7 +593,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
             }
             __syncthreads();
             // merge: ln g <- mean over the window's walkers (nearest 2^-32, ties
-            // to even), H <- 0
+            // to even); the next stage starts from it (lng0 <- ln g, H <- 0)
             for (int i = tid; i < n_win * w; i += nthreads) {
                 const int ww = i / w, bb = i - ww * w;
                 if (!wmerge_s[ww]) continue;
@@ -581,6 +602,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                 const long long mean = div_round_even(sacc, m);
                 for (int jj = 0; jj < m; ++jj) {
                     lng_s[(size_t)(ww * m + jj) * wg + kGuard + bb] = mean;
+                    lng0blk[(size_t)(ww * m + jj) * w + bb] = mean;
                     Hblk[(size_t)(ww * m + jj) * w + bb] = 0u;
                 }
             }

@@ -264,7 +264,8 @@ __global__ void features_kernel(DevState st, int inst, int first_sample, int n, 
 
 // ln g0 of every walker of window i: N s(E) over the realisable bins, shifted
 // so that the window's smallest value is 0, rounded to the 2^-32 grid;
-// H, latch reset; stage k0 (or frozen if k0 < 0)
+// the stage starts from it (lng0 = ln g, H = 0), latch reset; stage k0 (or
+// frozen if k0 < 0)
 __global__ void install_kernel(DevState st, int inst, const float *s_pred, int k0)
 {
     const InstDev I = st.inst[inst];
@@ -287,6 +288,7 @@ __global__ void install_kernel(DevState st, int inst, const float *s_pred, int k
         for (int j = 0; j < I.m; ++j) {
             const long long off = I.lng_off + (long long)(i * I.m + j) * w + b;
             st.lng[off] = units;
+            st.lng0[off] = units;
             st.H[off] = 0u;
         }
     }

@@ -45,8 +45,10 @@ def training_set(ctx, instances):
     return np.concatenate(X), np.concatenate(T)
 
 
-def train(net, X, T, steps=3000, batch=4096, lr=2e-3, seed=0, log_every=0):
-    """Adam on seeded mini-batches; returns the loss history (every log_every steps)."""
+def train(net, X, T, steps=3000, batch=4096, lr=2e-3, seed=0, log_every=0, lr_end=None):
+    """Adam on seeded mini-batches; returns the loss history (every log_every
+    steps).  With lr_end the step size follows a cosine from lr down to lr_end
+    over the run, which settles the last steps' mini-batch noise."""
     import torch
 
     rng = np.random.default_rng(seed)
@@ -60,7 +62,8 @@ def train(net, X, T, steps=3000, batch=4096, lr=2e-3, seed=0, log_every=0):
         xb = Xd.index_select(0, idx).contiguous()
         tb = Td.index_select(0, idx).contiguous()
         want = bool(log_every) and (it % log_every == 0 or it == steps - 1)
-        loss = net.train_step(xb, tb, lr, want_loss=want)
+        step_lr = lr if lr_end is None else lr_end + 0.5 * (lr - lr_end) * (1.0 + math.cos(math.pi * it / max(1, steps - 1)))
+        loss = net.train_step(xb, tb, step_lr, want_loss=want)
         if want:
             hist.append((it, loss))
     return hist
