@@ -130,6 +130,7 @@ int sweep_smem_bytes(int n_walkers, int n_win, int w, int lat_words)
     b += ((long long)n_win * w + 15) / 16 * 16;         // reach
     b += (long long)n_win * 16;                         // window state
     b += ((long long)n_walkers + 15) / 16 * 16;         // latch
+    b += 2LL * n_walkers * 4;                           // near masks, 2 slots
     return (int)b;
 }
 
@@ -146,20 +147,17 @@ struct Apb {
 // State-independent part of one trial, written by a producer warp into the
 // ring: byte offsets (from the start of the block's shared memory) of the
 // site's lattice word (Ising) or byte (Potts) and of its four neighbours'
-// (left, right, up, down); `aux` packs the bit positions of site, left and
-// right neighbour (Ising: x | x_l << 8 | x_r << 16, also as masks mx, ml,
-// mr) or the proposal offset (Potts: new value = old + aux mod q), and in
-// bit 24 the flag `near`: the
-// previous trial of the walker touched this trial's site or a neighbour (or
-// it is unknown), so values read before the previous move may be stale.
-// `lam` is the acceptance threshold.
+// (left, right, up, down); `aux` holds the bit position of the site (Ising;
+// the masks mx, ml, mr select site / up / down, left and right bits) or the
+// proposal offset (Potts: new value = old + aux mod q).  `lam` is the
+// acceptance threshold.  Trials whose site or a neighbour is the previous
+// trial's site ("near") are marked in a per-round bit mask beside the ring.
 struct __align__(16) Trial {
     uint32_t a_s, a_l, a_r, a_u, a_d, aux;
     long long lam;
     uint32_t mx, ml, mr, pad;   // Ising: bit masks of site (and up/down), left, right
 };
 
-static constexpr uint32_t kNear = 1u << 24;
 static_assert(sizeof(Trial) == 48, "ring records are 48 bytes");
 
 __device__ __forceinline__ bool site_near(int prev, int site, const Site &s, int L)
@@ -168,14 +166,15 @@ __device__ __forceinline__ bool site_near(int prev, int site, const Site &s, int
            prev == s.yd * L + s.x;
 }
 
-// The APB trials of one Philox block.  The first trial's `near` flag is set
-// (predecessor unknown) and cleared by the caller once the predecessor is
-// known; *first / *last receive the block's first and last sites.
+// The APB trials of one Philox block; *first / *last receive the block's
+// first and last sites, and the return value has bit k set when trial k > 0
+// is near trial k - 1 (the caller decides for trial 0).
 template <int MODEL>
-__device__ __forceinline__ void make_trials(Trial *out, unsigned long long blk, uint32_t c2, const InstDev &I,
-                                            uint32_t lat_off, int *first, int *last)
+__device__ __forceinline__ uint32_t make_trials(Trial *out, unsigned long long blk, uint32_t c2, const InstDev &I,
+                                                uint32_t lat_off, int *first, int *last)
 {
     int prev = -1;
+    uint32_t near_bits = 0;
     const u32x4 r = philox10((uint32_t)blk, (uint32_t)(blk >> 32), c2, 0u, I.key0, I.key1);
     if (MODEL == kIsing) {
         const uint32_t rs[2] = {r.x, r.z}, ru[2] = {r.y, r.w};
@@ -191,9 +190,8 @@ __device__ __forceinline__ void make_trials(Trial *out, unsigned long long blk, 
             t.a_r = row + 4u * (uint32_t)(s.xr >> 5);
             t.a_u = lat_off + 4u * (uint32_t)(s.yu * I.wpr) + hx;
             t.a_d = lat_off + 4u * (uint32_t)(s.yd * I.wpr) + hx;
-            const bool near = prev < 0 || site_near(prev, site, s, I.L);
-            t.aux = (uint32_t)(s.x & 31) | ((uint32_t)(s.xl & 31) << 8) | ((uint32_t)(s.xr & 31) << 16) |
-                    (near ? kNear : 0u);
+            if (prev >= 0 && site_near(prev, site, s, I.L)) near_bits |= 1u << k;
+            t.aux = (uint32_t)(s.x & 31);
             t.mx = 1u << (s.x & 31);
             t.ml = 1u << (s.xl & 31);
             t.mr = 1u << (s.xr & 31);
@@ -214,14 +212,14 @@ __device__ __forceinline__ void make_trials(Trial *out, unsigned long long blk, 
         t.a_r = lat_off + (uint32_t)s.y * L + (uint32_t)s.xr;
         t.a_u = lat_off + (uint32_t)s.yu * L + (uint32_t)s.x;
         t.a_d = lat_off + (uint32_t)s.yd * L + (uint32_t)s.x;
-        const bool near = prev < 0 || site_near(prev, site, s, I.L);
-        t.aux = (1u + scale_u32(r.y, (uint32_t)(I.q - 1))) | (near ? kNear : 0u);
+        t.aux = 1u + scale_u32(r.y, (uint32_t)(I.q - 1));
         t.mx = t.ml = t.mr = t.pad = 0u;
         t.lam = lam_threshold(r.z >> 8);
         out[0] = t;
         *first = site;
         *last = site;
     }
+    return near_bits;
 }
 
 // Lattice words (Ising) or values (Potts) a trial reads: site, left, right, up, down.
@@ -319,11 +317,13 @@ enum : int { kBarFull = 1, kBarEmpty = 3 };  // ids 1, 2 (full) and 3, 4 (empty)
 // state-independent parts of each trial, one round (kR trials per walker)
 // ahead of the consumer, handing slots over with named barriers.  The
 // consumer keeps the trial chain short: the next trial's lattice values are
-// read one trial ahead and its bin change is computed for both outcomes of
-// the current trial; ln g of the reachable bins is read before the bin change
-// is known.  H needs no per-trial work while ln f > 0 (it is read off ln g
-// and its value at the stage start); converged windows count it in global
-// memory with fire-and-forget reductions.
+// read one trial ahead, before the current trial's move is stored, and its
+// bin change is computed from them, so the current trial only waits for one
+// ln g load.  A trial whose site or a neighbour is the previous trial's site
+// (marked by the producers) ends the unrolled loop; lanes whose previous
+// trial moved read its values again there.  H needs no per-trial work while
+// ln f > 0 (it is read off ln g and its value at the stage start); converged
+// windows count it in global memory with fire-and-forget reductions.
 template <int MODEL>
 __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkItem *items, SweepArgs args)
 {
@@ -354,6 +354,8 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
     int *wmerge_s = wst_s + 2 * n_win;
     int *wgwin_s = wst_s + 3 * n_win;
     uint8_t *latch_s = reinterpret_cast<uint8_t *>(wst_s + 4 * n_win);
+    // per slot and walker: bit a set when trial a of the round is near trial a - 1
+    uint32_t *nearm_s = reinterpret_cast<uint32_t *>(latch_s + (nw + 15) / 16 * 16);
 
     const int slot_base = I.slot0 + it.win_begin * m;
     uint32_t *Hblk = st.H + I.lng_off + (long long)it.win_begin * m * w;   // this block's histograms
@@ -380,6 +382,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
         wconv_s[i] = st.conv[gwin];
         wmerge_s[i] = 0;
     }
+    for (int i = tid; i < 2 * nw; i += nthreads) nearm_s[i] = 0u;
     for (int i = tid; i < nw; i += nthreads) {
         latch_s[i] = st.latch[slot_base + i];
         draw_s[i] = st.draw[slot_base + i];
@@ -401,33 +404,40 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
     for (long sw = 0; sw < args.n_sweeps; ++sw) {
         if (!consumer) {
             // ---------------- producers ----------------
-            const int ptid = tid - 32;
+            // producer warp pw fills the records of walkers [w0, w0 + cw): task
+            // tk of a round is Philox block tk / cw of walker w0 + tk % cw, so
+            // consecutive lanes write consecutive ring records (no bank
+            // conflicts) and the block before a task's block is task tk - cw,
+            // held by this warp in this pass or the previous one
+            const int n_pw = nthreads / 32 - 1, pw = warp - 1;
+            const int w0 = pw * nw / n_pw, cw = (pw + 1) * nw / n_pw - w0;
+            const int src = lane >= cw ? lane - cw : lane + 32 - cw;
             for (int k = 0; k < rounds; ++k) {
                 const int slot = k & 1;
                 if (k >= 2) named_sync(kBarEmpty + slot, nthreads);
                 const int cnt = min(kR, N - k * kR);
                 const int nblk = cnt / APB;
-                const int total = nw * nblk;
-                for (int base = 0; base < total; base += n_prod) {
-                    const int task = base + ptid;
+                const int total = cw * nblk;
+                int last_prev = -1;
+                for (int base = 0; base < total; base += 32) {
+                    const int task = base + lane;
                     const bool act = task < total;
                     const int tk = act ? task : total - 1;
-                    // walker-fastest task order: consecutive lanes write
-                    // consecutive records of the ring (no bank conflicts)
-                    const int bi = tk / nw, wk = tk - bi * nw;
+                    const int bi = tk / cw, wk = w0 + (tk - bi * cw);
                     const int wlk = wk / m, jk = wk - wlk * m;
                     const uint32_t c2 = ((uint32_t)(it.win_begin + wlk) << 16) | (uint32_t)jk;
                     const unsigned long long blk = draw_s[wk] + (unsigned long long)(k * (kR / APB) + bi);
                     Trial tr[APB];
                     int first, last;
-                    make_trials<MODEL>(tr, blk, c2, I, lat_base + 4u * (uint32_t)(wk * lwp), &first, &last);
-                    // the trial before the block's first one is the last trial of
-                    // the lane nw below, which holds the walker's previous block
-                    // when it is in the same warp and pass
-                    const int from_left = __shfl_up_sync(0xffffffffu, last, nw < 32 ? nw : 0);
-                    if (nw < 32 && lane >= nw && bi > 0) {
+                    uint32_t nbits = make_trials<MODEL>(tr, blk, c2, I, lat_base + 4u * (uint32_t)(wk * lwp), &first, &last);
+                    // the block's first trial against the last trial of the
+                    // walker's previous block (none for the round's first
+                    // block: the consumer reads that trial's values afresh)
+                    const int p_same = __shfl_sync(0xffffffffu, last, src);
+                    const int p_prev = __shfl_sync(0xffffffffu, last_prev, src);
+                    if (bi > 0) {
                         const Site fs = site_of(first, I.L, I.magic_L);
-                        if (!site_near(from_left, first, fs, I.L)) tr[0].aux &= ~kNear;
+                        if (site_near(lane >= cw ? p_same : p_prev, first, fs, I.L)) nbits |= 1u;
                     }
                     if (act) {
                         // ring layout [slot][trial][walker]: the consumer lanes
@@ -435,7 +445,9 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                         Trial *dst = ring + ((size_t)slot * kR + bi * APB) * nw + wk;
 #pragma unroll
                         for (int i = 0; i < APB; ++i) dst[(size_t)i * nw] = tr[i];
+                        if (nbits) atomicOr(nearm_s + slot * nw + wk, nbits << (bi * APB));
                     }
+                    last_prev = last;
                 }
                 named_arrive(kBarFull + slot, nthreads);
             }
@@ -460,33 +472,29 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                     named_sync(kBarFull + slot, nthreads);
                     const int cnt = min(kR, N - k * kR);
                     const Trial *rr = ring + (size_t)slot * kR * nw + tv;   // record a at rr[a * nw]
+                    // trials near their predecessor in any lane end a run of
+                    // the loop below; the mask is cleared for the slot's next use
+                    uint32_t nm = 0u;
+                    if (valid) {
+                        nm = nearm_s[slot * nw + tv];
+                        nearm_s[slot * nw + tv] = 0u;
+                    }
+                    const uint32_t wm = __reduce_or_sync(0xffffffffu, nm);
                     Trial t = rr[0];
                     Trial t1 = rr[cnt > 1 ? nw : 0];
                     const Nbr n0 = load_nbr<MODEL>(smem, t);
                     int db = bin_change<MODEL>(n0, t, q);     // bin change of the current trial
                     uint32_t sv = n0.s;                        // its site word (Ising) / value (Potts)
                     bool acc_prev = false;
+                    int a = 0;
+                    for (;;) {
+                    const uint32_t later = wm & (0xFFFFFFFEu << a);   // near trials after a
+                    const int a_end = later ? __ffs(later) - 1 : cnt;
     #pragma unroll 3
-                    for (int a = 0; a < cnt; ++a) {
+                    for (; a < a_end; ++a) {
                         const Trial t2 = rr[(size_t)(a + 2 < cnt ? a + 2 : cnt - 1) * nw];
                         // the next trial's lattice values, read before this trial's move
                         const Nbr nn = load_nbr<MODEL>(smem, t1);
-                        // ln g of every bin a move can reach, before the move is known
-                        const long long sm1 = lng[b - 1], sp1 = lng[b + 1], sm2 = lng[b - 2], sp2 = lng[b + 2];
-                        long long sm3 = 0, sp3 = 0, sm4 = 0, sp4 = 0;
-                        if (MODEL == kPotts) {
-                            sm3 = lng[b - 3];
-                            sp3 = lng[b + 3];
-                            sm4 = lng[b - 4];
-                            sp4 = lng[b + 4];
-                        }
-                        // rare: the previous trial moved this trial's site or a
-                        // neighbour after db and sv were taken -- read them again
-                        if (acc_prev && (t.aux & kNear)) {
-                            const Nbr nf = load_nbr<MODEL>(smem, t);
-                            db = bin_change<MODEL>(nf, t, q);
-                            sv = nf.s;
-                        }
                         // this trial's move: Ising flips one bit of the site word,
                         // Potts writes the new value
                         uint32_t moved;
@@ -501,18 +509,9 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                         const int bn = b + db;
                         const bool inw = (unsigned)(bn - lo) < (unsigned)w;
                         const long long thr = cur + t.lam;
-                        long long v;
-                        if (MODEL == kIsing) {
-                            const long long p1 = db < 0 ? sm1 : sp1, p2 = db < 0 ? sm2 : sp2;
-                            v = (db & 1) ? p1 : p2;
-                        } else {
-                            const int ad = db < 0 ? -db : db;
-                            const long long p1 = db < 0 ? sm1 : sp1, p2 = db < 0 ? sm2 : sp2;
-                            const long long p3 = db < 0 ? sm3 : sp3, p4 = db < 0 ? sm4 : sp4;
-                            const long long p12 = (ad & 1) ? p1 : p2, p34 = (ad & 1) ? p3 : p4;
-                            v = ad > 2 ? p34 : p12;
-                        }
-                        v = db == 0 ? cur : v;
+                        // ln g of the proposed bin (shared memory holds cur at b,
+                        // and guard cells beyond the window's edges)
+                        const long long v = lng[bn];
                         const bool acc = inw && (v < thr);
                         if (MODEL == kIsing) st_shared_u32_if(valid && acc, sbase + t.a_s, moved);
                         else st_shared_u8_if(valid && acc, sbase + t.a_s, moved);
@@ -537,6 +536,15 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                         sv = sv_next;
                         t = t1;
                         t1 = t2;
+                    }
+                    if (a >= cnt) break;
+                    // trial a is near trial a - 1 in some lane: where that trial
+                    // moved, db and sv were taken before the move -- read again
+                    if (acc_prev && ((nm >> a) & 1u)) {
+                        const Nbr nf = load_nbr<MODEL>(smem, t);
+                        db = bin_change<MODEL>(nf, t, q);
+                        sv = nf.s;
+                    }
                     }
                     if (k + 2 < rounds) named_arrive(kBarEmpty + slot, nthreads);
                 }
