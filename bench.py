@@ -2,15 +2,18 @@
 Wang-Landau path on the batched 2D Ising workload (L = 32 and L = 64, 16
 windows x 4 walkers per window at 75 % overlap, 32 seeds per size, exchange
 every 10^4 sweeps) -- one step = 10^4 sweeps of every walker plus one exchange
-phase, replayed from the library's CUDA graph.
+phase.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line.  `value` is device-timed (CUDA events on the library's
-stream, L2 flushed between steps); `e2e` is wall-clock through the public API
-with host descriptors in and ln g pieces out every step; `roofline` relates the
-sweep kernel's issue rate to the GPU's thread-instruction peak; `cpu_baseline`
-is the CPU oracle on the host cores on a bounded sample of the same workload.
+stream around rewl_run + rewl_exchange, L2 flushed between steps); `e2e` is
+wall-clock through the public API (the CUDA-graph cycle rewl_run_cycles) with
+host descriptors in and ln g pieces out every step; `roofline` relates the
+sweep launches' algorithmic instruction rate, timed by events around rewl_run
+inside the same timed steps, to the GPU's thread-instruction peak;
+`cpu_baseline` is the CPU oracle on the host cores on a bounded sample of the
+same workload.
 Under torchrun each rank runs its own batch (distinct seeds, weak scaling).
 """
 import argparse
@@ -181,37 +184,30 @@ def run_ours(args, rank, world):
     ctx = R.Rewl([R.instance(**d) for d in ds], stream=stream)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
-        ctx.run_cycles(1, SWEEPS_PER_STEP)
+        ctx.run(SWEEPS_PER_STEP)
+        ctx.exchange()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     launches0 = ctx.launch_count()
-    times = []
+    times, ks = [], []
     with ClockSampler(dev) as clk:
         for _ in range(args.steps):
             flush.fill_(1)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a, m, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             a.record(stream)
-            ctx.run_cycles(1, SWEEPS_PER_STEP)
+            ctx.run(SWEEPS_PER_STEP)       # sweep launches of every size class, joined on `stream`
+            m.record(stream)
+            ctx.exchange()
             b.record(stream)
             b.synchronize()
             times.append(a.elapsed_time(b) / 1000.0)
+            ks.append(a.elapsed_time(m) / 1000.0)
         torch.cuda.synchronize()
     launches = ctx.launch_count() - launches0
     t_step = max_over_ranks(sum(times) / len(times), world, device="cuda")
     value = attempts_per_step * world / t_step
     clocks = clk.summary()
-
-    # sweep-kernel launch duration alone (CUDA events on the library's stream)
-    ks = []
-    for _ in range(3):
-        flush.fill_(1)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        ctx.run(SWEEPS_PER_STEP)
-        b.record(stream)
-        b.synchronize()
-        ks.append(a.elapsed_time(b) / 1000.0)
     k_time = sum(ks) / len(ks)
     ctx.close()
 
@@ -264,6 +260,110 @@ def profile_case():
     print(json.dumps({"profile_case": "config1 batch, 2 x (20 sweeps + exchange)", "sweeps": st["sweeps"]}))
 
 
+def _golden_ising(L):
+    """Exact ln g of the L x L Ising model on its bin grid, from the fixture
+    written by tests/golden/make_golden.py (nan where no configuration)."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", f"ising_L{L}_exact_lng.txt")
+    rows = np.loadtxt(path, usecols=(0, 1))
+    N = L * L
+    out = np.full(N + 1, np.nan)
+    out[((rows[:, 0] + 2 * N) // 4).astype(int)] = rows[:, 1]
+    return out
+
+
+def _mean_rel_err(lg, ref):
+    import numpy as np
+    ok = np.isfinite(lg) & np.isfinite(ref) & (ref != 0)
+    return float(np.mean(np.abs(lg[ok] - ref[ok]) / np.abs(ref[ok])))
+
+
+def _log_sum(lg):
+    import numpy as np
+    v = lg[np.isfinite(lg)]
+    m = v.max()
+    return float(m + np.log(np.exp(v - m).sum()))
+
+
+def warm_start_workload(seeds=4, exchange_interval=1000, poll_cycles=5):
+    """Time to ln f = 2^-20, learned warm start vs plain REWL, on one GPU: the
+    network is trained on plain-REWL DOS at L = 8..48 (Ising and q=10 Potts),
+    then Ising L = 128 and q=10 Potts L = 64 (64 windows x 4 walkers, `seeds`
+    instances each in one batch) run to convergence from ln g = 0, ln f = 1
+    (plain) and from the network's ln g at ln f = 2^-4 (learned).  Reports wall
+    time, sweeps of each instance's slowest window (the MC time of Eq. (7)),
+    and the ln g error: Ising against the exact DOS, Potts against the plain
+    run's DOS and through ln sum g = N ln q."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1407_5140_gb300 import rewl as R
+    from paper_1407_5140_gb300 import warmstart as WS
+    from paper_1407_5140_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    t0 = time.perf_counter()
+    train = W.config4_training()
+    gen = R.Rewl([R.instance(**d) for d in train], stream=stream)
+    ok = gen.run_to_convergence(exchange_interval, 5_000_000, poll_cycles=poll_cycles)
+    t_gen = time.perf_counter() - t0
+    X, T = WS.training_set(gen, train)
+    gen.close()
+    t1 = time.perf_counter()
+    net = R.Mlp(max_batch=4096, seed=11, stream=stream)
+    hist = WS.train(net, X, T, steps=3000, batch=4096, lr=2e-3, seed=2, log_every=1000, lr_end=1e-4)
+    rms = float(np.sqrt(np.mean((WS.predict(net, X) - T) ** 2)))
+    t_train = time.perf_counter() - t1
+    out = {"metric": "time to ln f=2^-20, learned vs plain", "unit": "s", "n_gpus": 1, "data": "synthetic",
+           "training": {"instances": len(train), "converged": bool(ok), "samples": int(X.shape[0]),
+                        "generate_s": t_gen, "train_s": t_train, "train_steps": 3000,
+                        "rms_error_s_per_site": rms, "loss_history": hist},
+           "results": []}
+    for tgt in W.config4_targets():
+        L, model = tgt["L"], tgt["model"]
+        ds = [dict(tgt, seed=tgt["seed"] + k) for k in range(seeds)]
+        runs = {}
+        for mode in ("plain", "learned"):
+            ctx = R.Rewl([R.instance(**d) for d in ds], stream=stream)
+            ctx.run(1)                       # plan and first launch outside the timed region
+            torch.cuda.synchronize()
+            if mode == "learned":
+                for k in range(seeds):
+                    ctx.warm_start(k, net, 2.0 ** -4)
+            ts = time.perf_counter()
+            conv = ctx.run_to_convergence(exchange_interval, 20_000_000, poll_cycles=poll_cycles)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - ts
+            sweeps = [int(ctx.counters(k)["conv_sweep"].max()) for k in range(seeds)]
+            dos = [ctx.get_dos(k)[0] for k in range(seeds)]
+            runs[mode] = dict(seconds=secs, converged=bool(conv), sweeps_slowest_window=sweeps, dos=dos)
+            ctx.close()
+        res = {"instance": ("Ising" if model == R.ISING else "Potts q=10") + f" L={L}, 64 windows x 4 walkers",
+               "seeds": seeds}
+        for mode, r in runs.items():
+            ent = {"seconds": r["seconds"], "converged": r["converged"],
+                   "sweeps_slowest_window": r["sweeps_slowest_window"],
+                   "mean_sweeps": float(np.mean(r["sweeps_slowest_window"]))}
+            if model == R.ISING:
+                ex = _golden_ising(L)
+                ent["eps_vs_exact"] = [_mean_rel_err(lg, ex) for lg in r["dos"]]
+            else:
+                ent["log_sum_minus_N_ln_q"] = [_log_sum(lg) - L * L * math.log(10) for lg in r["dos"]]
+            res[mode] = ent
+        if model != R.ISING:
+            res["learned"]["eps_vs_plain"] = [_mean_rel_err(a, b) for a, b in
+                                             zip(runs["learned"]["dos"], runs["plain"]["dos"])]
+            res["plain"]["eps_seed_to_seed"] = [_mean_rel_err(runs["plain"]["dos"][k], runs["plain"]["dos"][0])
+                                               for k in range(1, seeds)]
+        res["sweep_ratio_learned_over_plain"] = res["learned"]["mean_sweeps"] / res["plain"]["mean_sweeps"]
+        res["time_ratio_learned_over_plain"] = res["learned"]["seconds"] / res["plain"]["seconds"]
+        out["results"].append(res)
+    net.close()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,9 +373,14 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--profile-case", action="store_true",
                     help="only the workload's launch shape with 20 sweeps per launch (for ncu captures)")
+    ap.add_argument("--workload", default="throughput", choices=["throughput", "warm-start"],
+                    help="warm-start: time to converge, learned vs plain (Ising L=128, Potts q=10 L=64)")
     args = ap.parse_args()
     if args.profile_case:
         profile_case()
+        return
+    if args.workload == "warm-start":
+        warm_start_workload()
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -67,8 +67,11 @@ typedef struct rewl_instance {
     int64_t e_min, e_max;       /* inclusive energy range, on the bin grid      */
     double overlap;             /* o in [0, 1)                                  */
     int32_t walkers_per_window; /* m, 1..32                                     */
-    int32_t reserved;
-    double flatness;            /* p in (0, 1]: flat iff min H >= p <H>         */
+    int32_t flat_rule;          /* 0: flat iff min H >= p <H> (Sec. II A);
+                                 * 1: Zhou-Bhatt, flat iff min H >= a/sqrt(ln f)
+                                 *    (Sec. IV B, Eq. (8)), a = flatness; both
+                                 *    over the window's realisable bins       */
+    double flatness;            /* rule 0: p in (0, 1]; rule 1: a in (0, 1e6]  */
     double ln_f_final;          /* run ends after the stage with ln f <= this   */
     uint64_t seed;              /* Philox key                                   */
     uint32_t instance_id;       /* xor-ed into the key's high word              */

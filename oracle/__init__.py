@@ -46,6 +46,9 @@ def lib():
         L.oracle_get_counters.argtypes = [vp] * 7
         L.oracle_all_converged.argtypes = [vp]
         L.oracle_set_check_every.argtypes = [vp, i64]
+        L.oracle_set_flat_rule.argtypes = [vp, C.c_int]
+        L.oracle_zb_flat.argtypes = [C.c_uint64, C.c_double, C.c_int]
+        L.oracle_zb_flat.restype = C.c_int
         L.oracle_error.argtypes = [vp]
         L.oracle_energy_of.argtypes = [vp, i32]
         L.oracle_energy_of.restype = i64
@@ -77,6 +80,11 @@ def philox(key, counters):
     return out
 
 
+def zb_flat(min_h, a, stage):
+    """The oracle's Zhou-Bhatt decision (Eq. (8)) for one walker."""
+    return bool(lib().oracle_zb_flat(int(min_h), float(a), int(stage)))
+
+
 def lam_fix(k):
     """Acceptance threshold max(1, trunc(2^32 * -ln((k+1) 2^-24))) of the oracle."""
     k = np.ascontiguousarray(k, dtype=np.uint32)
@@ -89,7 +97,7 @@ class Oracle:
     """One REWL instance: h windows x m walkers on an L x L lattice."""
 
     def __init__(self, model, L, q, e_min, e_max, n_windows, overlap, walkers_per_window,
-                 flatness=0.8, ln_f_final=2.0 ** -20, seed=0, instance=0, threads=0):
+                 flatness=0.8, ln_f_final=2.0 ** -20, seed=0, instance=0, threads=0, flat_rule=0):
         self.model, self.L, self.q = model, L, (2 if model == ISING else q)
         self.N = L * L
         self.h, self.m = n_windows, walkers_per_window
@@ -98,6 +106,7 @@ class Oracle:
                                       walkers_per_window, flatness, ln_f_final, seed, instance)
         if not self._o:
             raise ValueError("oracle_create rejected the parameters")
+        lib().oracle_set_flat_rule(self._o, flat_rule)
         B = np.zeros(1, np.int32)
         w = np.zeros(1, np.int32)
         lib().oracle_geometry(self._o, _p(B), _p(w), None, None)

@@ -32,6 +32,10 @@
  *     bin is updated.
  *   - flatness is tested after every sweep (N attempts) on the reachable
  *     bins of the window: flat iff min(H) * n_reach >= p * sum(H) (FP64).
+ *     With the Zhou-Bhatt rule (Sec. IV B, Eq. (8)) the same parameter is a
+ *     and a walker is flat iff min(H) >= a / sqrt(ln f); with ln f = 2^-k
+ *     that is min(H) >= sqrt(2^k a^2), evaluated as sqrt(ldexp(a * a, k))
+ *     (each step a correctly rounded IEEE-754 double operation).
  *     A flat walker latches and keeps walking with the same ln f.
  *   - when all m walkers of a window are latched, their ln g are replaced by
  *     the mean, rounded to the nearest multiple of 2^-32 (ties to even);
@@ -139,6 +143,7 @@ typedef struct {
     unsigned char *reach;     /* reach[b]: energy of bin b is realisable     */
     int *n_reach;             /* reachable bins in each window               */
     double p_flat, ln_f_final;
+    int flat_rule;            /* 0: min H >= p <H>;  1: min H >= a/sqrt(ln f)  */
     long check_every;         /* sweeps between flatness tests               */
     uint32_t key0, key1;
     int n_walkers;            /* h * m, walker id = window * m + j           */
@@ -429,8 +434,14 @@ static void walker_sweep(rewl_oracle *o, int k)
     }
 }
 
+/* Zhou-Bhatt test (Eq. (8)): min H >= a / sqrt(ln f) with ln f = 2^-stage */
+int oracle_zb_flat(uint64_t min_h, double a, int stage)
+{
+    return (double)min_h >= sqrt(ldexp(a * a, stage));
+}
+
 /* flatness test (Sec. II A): no H(E) below p times the mean of H over the
- * reachable bins of the walker's window */
+ * reachable bins of the walker's window (or the Zhou-Bhatt minimum) */
 static int walker_flat(const rewl_oracle *o, int k)
 {
     int win = k / o->m, lo = o->lo[win];
@@ -441,6 +452,7 @@ static int walker_flat(const rewl_oracle *o, int k)
         if (H[b] < mn) mn = H[b];
         sum += H[b];
     }
+    if (o->flat_rule == 1) return oracle_zb_flat(mn, o->p_flat, o->stage[win]);
     return (double)mn * (double)o->n_reach[win] >= o->p_flat * (double)sum;
 }
 
@@ -619,6 +631,9 @@ void oracle_get_counters(const rewl_oracle *o, long *sweeps, uint64_t *t_exch, u
 }
 
 void oracle_set_check_every(rewl_oracle *o, long c) { o->check_every = c > 0 ? c : 1; }
+
+/* 0: fraction-of-mean flatness (Sec. II A); 1: Zhou-Bhatt minimum (Eq. (8)) */
+void oracle_set_flat_rule(rewl_oracle *o, int rule) { o->flat_rule = rule == 1 ? 1 : 0; }
 
 int oracle_all_converged(const rewl_oracle *o)
 {

@@ -124,7 +124,9 @@ static rewl_status build_instance(const rewl_instance &d, HostInst &hi, std::str
     if (d.n_windows < 1 || d.n_windows > 65535) { why = "n_windows must be in 1..65535"; return REWL_EINVAL; }
     if (d.walkers_per_window < 1 || d.walkers_per_window > 32) { why = "walkers_per_window must be in 1..32"; return REWL_EINVAL; }
     if (!(d.overlap >= 0.0 && d.overlap < 1.0)) { why = "overlap must be in [0, 1)"; return REWL_EINVAL; }
-    if (!(d.flatness > 0.0 && d.flatness <= 1.0)) { why = "flatness must be in (0, 1]"; return REWL_EINVAL; }
+    if (d.flat_rule != 0 && d.flat_rule != 1) { why = "flat_rule must be 0 (fraction of mean) or 1 (Zhou-Bhatt)"; return REWL_EINVAL; }
+    if (d.flat_rule == 0 && !(d.flatness > 0.0 && d.flatness <= 1.0)) { why = "flatness must be in (0, 1]"; return REWL_EINVAL; }
+    if (d.flat_rule == 1 && !(d.flatness > 0.0 && d.flatness <= 1e6)) { why = "Zhou-Bhatt a must be in (0, 1e6]"; return REWL_EINVAL; }
     if (!(d.ln_f_final >= std::ldexp(1.0, -32) && d.ln_f_final <= 1.0)) { why = "ln_f_final must be in [2^-32, 1]"; return REWL_EINVAL; }
     const long long N = (long long)d.L * d.L;
     const int step = d.model == REWL_ISING ? 4 : 1;
@@ -175,6 +177,7 @@ static rewl_status build_instance(const rewl_instance &d, HostInst &hi, std::str
     I.key0 = (uint32_t)d.seed;
     I.key1 = (uint32_t)(d.seed >> 32) ^ d.instance_id;
     I.p_flat = d.flatness;
+    I.flat_rule = d.flat_rule;
     return REWL_OK;
 }
 

@@ -41,8 +41,9 @@ struct InstDev {
     int64_t lng_off;      // element offset of walker 0's ln g / H
     int64_t lat_off;      // word offset of configuration 0
     uint32_t key0, key1;  // Philox key
-    double p_flat;
-    int32_t pad0, pad1;
+    double p_flat;        // rule 0: p; rule 1: a
+    int32_t flat_rule;    // 0: min H >= p <H>; 1: min H >= a / sqrt(ln f)
+    int32_t pad1;
 };
 
 // One thread block of the sweep kernel: n_win consecutive windows of one instance.

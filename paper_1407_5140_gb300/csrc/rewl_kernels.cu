@@ -463,8 +463,10 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
             // the rounds of one sweep; kCountH adds the H counting of
             // converged windows, compiled out where the warp has none: a run
             // of trials that end in the same bin is added to H when the walker
-            // leaves the bin (and at the end of the sweep)
-            uint32_t run = 0;
+            // leaves the bin (and at the end of the sweep), one trial later
+            uint32_t run = 0, prun = 0;
+            bool pend = false;
+            uint32_t *Hpend = H;
             auto sweep_rounds = [&](auto count_h) {
                 constexpr bool kCountH = decltype(count_h)::value;
                 for (int k = 0; k < rounds; ++k) {
@@ -493,6 +495,8 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
     #pragma unroll 3
                     for (; a < a_end; ++a) {
                         const Trial t2 = rr[(size_t)(a + 2 < cnt ? a + 2 : cnt - 1) * nw];
+                        // the previous trial's H flush, its operands long ready
+                        if (kCountH) red_add_global_u32_if(pend, Hpend, prun);
                         // the next trial's lattice values, read before this trial's move
                         const Nbr nn = load_nbr<MODEL>(smem, t1);
                         // this trial's move: Ising flips one bit of the site word,
@@ -524,7 +528,9 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                         if (MODEL == kIsing) sv_next ^= (acc && t1.a_s == t.a_s) ? t.mx : 0u;
                         if (kCountH) {
                             const bool leave = acc && db != 0;
-                            red_add_global_u32_if(valid && frozen && leave, H + b, run);
+                            pend = valid && frozen && leave;
+                            Hpend = H + b;
+                            prun = run;
                             run = leave ? 1u : run + 1u;
                         }
                         b = acc ? bn : b;
@@ -551,6 +557,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
             };
             if (__any_sync(0xffffffffu, valid && frozen)) sweep_rounds(std::true_type{});
             else sweep_rounds(std::false_type{});
+            red_add_global_u32_if(pend, Hpend, prun);
             red_add_global_u32_if(valid && frozen && run != 0u, H + b, run);
             n_acc += acc_count;
         }
@@ -589,8 +596,12 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                 if (lane == 0) {
                     if (amax >= (1LL << 53)) atomicOr(st.error, kErrRange);
                     const int n_reach = st.n_reach[I.win0 + it.win_begin + wlk];
-                    if (!wconv_s[wlk] && !latch_s[wk] && (double)mn * (double)n_reach >= I.p_flat * (double)sum)
-                        latch_s[wk] = 1;
+                    // Sec. II A: min H >= p <H>; Eq. (8): min H >= a / sqrt(ln f),
+                    // ln f = 2^-stage, as sqrt(ldexp(a * a, stage)) in IEEE doubles
+                    const bool flat = I.flat_rule == 1
+                                          ? (double)mn >= sqrt(ldexp(I.p_flat * I.p_flat, wstage_s[wlk]))
+                                          : (double)mn * (double)n_reach >= I.p_flat * (double)sum;
+                    if (!wconv_s[wlk] && !latch_s[wk] && flat) latch_s[wk] = 1;
                 }
             }
             __syncthreads();

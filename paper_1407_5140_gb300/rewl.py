@@ -29,7 +29,7 @@ class RewlError(RuntimeError):
 class rewl_instance(C.Structure):
     _fields_ = [("model", C.c_int32), ("L", C.c_int32), ("q", C.c_int32), ("n_windows", C.c_int32),
                 ("e_min", C.c_int64), ("e_max", C.c_int64), ("overlap", C.c_double),
-                ("walkers_per_window", C.c_int32), ("reserved", C.c_int32), ("flatness", C.c_double),
+                ("walkers_per_window", C.c_int32), ("flat_rule", C.c_int32), ("flatness", C.c_double),
                 ("ln_f_final", C.c_double), ("seed", C.c_uint64), ("instance_id", C.c_uint32),
                 ("reserved2", C.c_uint32)]
 
@@ -111,13 +111,13 @@ def _stream_ptr(stream):
 
 
 def instance(model, L, q=2, e_min=None, e_max=None, n_windows=1, overlap=0.75, walkers_per_window=1,
-             flatness=0.8, ln_f_final=2.0 ** -20, seed=0, instance_id=0):
+             flatness=0.8, ln_f_final=2.0 ** -20, seed=0, instance_id=0, flat_rule=0):
     N = L * L
     if e_min is None:
         e_min = -2 * N
     if e_max is None:
         e_max = 2 * N if model == ISING else 0
-    return rewl_instance(model, L, q, n_windows, e_min, e_max, overlap, walkers_per_window, 0, flatness,
+    return rewl_instance(model, L, q, n_windows, e_min, e_max, overlap, walkers_per_window, flat_rule, flatness,
                          ln_f_final, seed, instance_id, 0)
 
 

@@ -10,11 +10,12 @@ import numpy as np
 ISING, POTTS = 0, 1
 
 
-def _inst(model, L, q, h, m, seed, instance_id=0, overlap=0.75, flatness=0.8, ln_f_final=2.0 ** -20):
+def _inst(model, L, q, h, m, seed, instance_id=0, overlap=0.75, flatness=0.8, ln_f_final=2.0 ** -20,
+          flat_rule=0):
     N = L * L
     return dict(model=model, L=L, q=q, e_min=-2 * N, e_max=(2 * N if model == ISING else 0), n_windows=h,
                 overlap=overlap, walkers_per_window=m, flatness=flatness, ln_f_final=ln_f_final, seed=seed,
-                instance_id=instance_id)
+                instance_id=instance_id, flat_rule=flat_rule)
 
 
 def config0():
@@ -49,6 +50,24 @@ def config3(seed=3):
         L = int(rng.choice([16, 24, 32]))
         out.append(_inst(POTTS, L, 10, _h(L), _m(L), 2000 + k))
     return out
+
+
+def config4_training(seeds=2):
+    """Plain-REWL runs the warm-start network learns from: Ising and q=10 Potts
+    at L = 8, 16, 24, 32, 48 (windows and walkers as in the uneven batch), run
+    to ln f = 2^-14."""
+    out = []
+    for L in (8, 16, 24, 32, 48):
+        for s in range(seeds):
+            out.append(_inst(ISING, L, 2, _h(L), _m(L), 4000 + 10 * L + s, ln_f_final=2.0 ** -14))
+            out.append(_inst(POTTS, L, 10, _h(L), _m(L), 5000 + 10 * L + s, ln_f_final=2.0 ** -14))
+    return out
+
+
+def config4_targets():
+    """Warm-start targets: 2D Ising L = 128 and q=10 Potts L = 64, each 64
+    windows x 4 walkers at 75 % overlap, ln f_final = 2^-20."""
+    return [_inst(ISING, 128, 2, 64, 4, 6128), _inst(POTTS, 64, 10, 64, 4, 7064)]
 
 
 def _h(L):

@@ -8,7 +8,7 @@ import oracle as O
 def make_oracle(d, threads=0):
     return O.Oracle(d["model"], d["L"], d["q"], d["e_min"], d["e_max"], d["n_windows"], d["overlap"],
                     d["walkers_per_window"], d["flatness"], d["ln_f_final"], seed=d["seed"],
-                    instance=d["instance_id"], threads=threads)
+                    instance=d["instance_id"], threads=threads, flat_rule=d.get("flat_rule", 0))
 
 
 def make_gpu(ds, **opts):

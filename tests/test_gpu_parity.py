@@ -151,6 +151,39 @@ def test_full_convergence_config0_bit_exact_and_accurate():
     assert eps < 0.03, eps
 
 
+@pytest.mark.parametrize("d", [_ising(8, 4, 4, seed=31, flat_rule=1, flatness=1.0),
+                               _potts(6, 3, 3, 2, seed=32, flat_rule=1, flatness=2.0),
+                               _ising(16, 5, 3, seed=33, flat_rule=1, flatness=0.5)],
+                         ids=["ising_L8_a1", "potts_q3_L6_a2", "ising_L16_a0.5"])
+def test_zhou_bhatt_trajectories_match_oracle(d):
+    """Eq. (8) flatness (min H >= a / sqrt(ln f)) on both sides: the stage
+    sequence, merges and every other state element stay bit-exact."""
+    gpu = make_gpu([d])
+    orc = make_oracle(d)
+    orc.init()
+    for c in range(6):
+        step_both(gpu, [orc], 150)
+        assert_same_state(gpu, 0, orc, f"cycle {c}")
+    assert int(np.max(orc.state()["stage"])) > 0        # the rule did end some iterations
+
+
+def test_zhou_bhatt_full_convergence_bit_exact():
+    """Config-0 shape with 4 walkers per window and the Eq. (8) rule (a = 1) run
+    to ln f = 2^-20 on both sides; bit-exact end state, DOS near the exact one."""
+    d = _ising(8, 4, 4, seed=1, flat_rule=1, flatness=1.0)
+    gpu = make_gpu([d])
+    orc = make_oracle(d)
+    orc.init()
+    for c in range(100):
+        step_both(gpu, [orc], 1000)
+        if orc.all_converged():
+            break
+    assert orc.all_converged() and gpu.status(0)["all_converged"]
+    assert_same_state(gpu, 0, orc, "zhou-bhatt converged")
+    lg, _ = gpu.get_dos(0)
+    assert cc.mean_relative_error(lg, _golden_lng(8, 65)) < 0.06
+
+
 def test_graph_cycles_equal_stepwise_calls():
     d = _ising(16, 4, 2, seed=21)
     a = make_gpu([d])
@@ -213,7 +246,8 @@ def test_config1_launch_sampled_instances_match_oracle():
 def test_invalid_arguments_fail_cleanly():
     from paper_1407_5140_gb300 import rewl as R
     for bad in [dict(L=7), dict(L=3), dict(n_windows=0), dict(overlap=1.0), dict(e_min=-130),
-                dict(e_min=-126), dict(ln_f_final=0.0)]:
+                dict(e_min=-126), dict(ln_f_final=0.0), dict(flatness=1.5), dict(flat_rule=2),
+                dict(flat_rule=1, flatness=0.0), dict(flat_rule=1, flatness=2e6)]:
         d = _ising(8, 4, 1)
         d.update(bad)
         with pytest.raises(R.RewlError) as ei:

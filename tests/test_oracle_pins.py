@@ -83,6 +83,30 @@ def test_ising_kaufman_invariants(L):
     assert g[-2 * N + 8] == 2 * N and g[-2 * N + 12] == 4 * N  # one / two flipped spins
 
 
+def test_prime_field_kaufman_matches_multiprecision_and_brute_force():
+    """The prime-field evaluation (exact integers by NTT + CRT) of the same closed
+    form agrees with brute force at L = 4 and with the multiprecision DFT at
+    L = 6..16 -- two independent ways of reading the coefficients off."""
+    assert ed.ising_kaufman_modular(4) == ed.ising_bruteforce(4)
+    for L in (6, 8, 10, 12, 16):
+        assert ed.ising_kaufman_modular(L) == ed.ising_kaufman(L), L
+
+
+@pytest.mark.parametrize("L", [32, 64])
+def test_prime_field_kaufman_invariants_large(L):
+    g = ed.ising_kaufman_modular(L)
+    N = L * L
+    assert sum(g.values()) == 2 ** N
+    assert all(g[E] == g.get(-E) for E in g)
+    assert sum(c * E * E for E, c in g.items()) == 2 * N * 2 ** N
+    assert g[-2 * N] == 2 and -2 * N + 4 not in g
+    assert g[-2 * N + 8] == 2 * N and g[-2 * N + 12] == 4 * N
+    # the fixture written for this size agrees (L = 32 from the multiprecision path)
+    rows = np.loadtxt(os.path.join(GOLDEN, f"ising_L{L}_exact_lng.txt"), usecols=(0, 1))
+    assert len(rows) == len(g)
+    assert max(abs(math.log(g[int(E)]) - lg) / max(1.0, lg) for E, lg in rows) < 1e-12   # 13 digits stored
+
+
 def test_golden_l8_is_kaufman():
     rows = np.loadtxt(os.path.join(GOLDEN, "ising_L8_exact_lng.txt"), dtype=object)
     g = ed.ising_kaufman(8)
@@ -356,6 +380,40 @@ def test_concatenate_reassembles_exact_pieces():
 # ---------------------------------------------------------------------------
 # warm-start network reference: chain-rule gradient against finite differences
 # ---------------------------------------------------------------------------
+def test_zhou_bhatt_decision_is_exact():
+    """Eq. (8): flat iff H >= a / sqrt(ln f) = a 2^(k/2) at ln f = 2^-k, i.e.
+    H^2 >= a^2 2^k -- checked in exact rational arithmetic around the
+    threshold for exactly representable a (ties included where a^2 2^k is a
+    perfect square)."""
+    from fractions import Fraction
+    for a in (1.0, 0.5, 2.5, 10.0, 0.1, 3.0):
+        for k in range(0, 33):
+            x = Fraction(a) ** 2 * 2 ** k
+            h0 = math.isqrt(int(math.ceil(x)))
+            for h in range(max(0, h0 - 2), h0 + 3):
+                assert O.zb_flat(h, a, k) == (h * h >= x), (a, k, h)
+
+
+def test_zhou_bhatt_rule_converges_faster_than_80_percent():
+    """Sec. IV B: with m walkers per window the Zhou-Bhatt minimum (a = 1)
+    ends WL iterations much sooner than the 80 % rule; the joined DOS still
+    converges to the exact one (Config-0 shape with m = 4)."""
+    ex = ed.log_dos_on_bins(ed.ising_kaufman(8), -128, 4, 65)
+    sweeps, eps = {}, {}
+    for rule, a in ((0, 0.8), (1, 1.0)):
+        sw, er = [], []
+        for seed in range(3):
+            o = O.Oracle(0, 8, 2, -128, 128, 4, 0.75, 4, flatness=a, seed=seed, flat_rule=rule)
+            o.init()
+            assert o.run_to_convergence(1000, 3_000_000)
+            sw.append(int(np.max(o.counters()["conv_sweep"])))
+            lg, _ = cc.concatenate(o.pieces(), o.lo, o.w, o.reach, 4.0, math.log(2))
+            er.append(cc.mean_relative_error(lg, ex))
+        sweeps[rule], eps[rule] = np.mean(sw), np.mean(er)
+    assert sweeps[1] < 0.4 * sweeps[0], sweeps
+    assert eps[1] < 0.05 and eps[0] < 0.02, eps
+
+
 def test_mlp_reference_gradient_matches_finite_differences():
     from oracle import mlp as M
     rng = np.random.default_rng(0)
