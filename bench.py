@@ -285,7 +285,22 @@ def _log_sum(lg):
     return float(m + np.log(np.exp(v - m).sum()))
 
 
-def warm_start_workload(seeds=4, exchange_interval=1000, poll_cycles=5):
+def _converge(ctx, exchange_interval, poll_cycles, cap_s, tag):
+    """run_to_convergence in chunks of 50 cycles with a wall-time cap; progress
+    (converged windows, ln f range) on stderr."""
+    import numpy as np
+    t0 = time.perf_counter()
+    while True:
+        done = ctx.run_to_convergence(exchange_interval, 50 * exchange_interval, poll_cycles=poll_cycles)
+        st = ctx.status(0)
+        lnf = st["ln_f"]
+        print(f"[{tag}] {time.perf_counter() - t0:7.1f} s, sweeps {st['sweeps']}, windows converged "
+              f"{int(np.sum(lnf == 0))}/{lnf.size} (instance 0)", file=sys.stderr, flush=True)
+        if done or time.perf_counter() - t0 > cap_s:
+            return done
+
+
+def warm_start_workload(seeds=4, exchange_interval=1000, poll_cycles=5, cap_s=900.0):
     """Time to ln f = 2^-20, learned warm start vs plain REWL, on one GPU: the
     network is trained on plain-REWL DOS at L = 8..48 (Ising and q=10 Potts),
     then Ising L = 128 and q=10 Potts L = 64 (64 windows x 4 walkers, `seeds`
@@ -307,7 +322,7 @@ def warm_start_workload(seeds=4, exchange_interval=1000, poll_cycles=5):
     t0 = time.perf_counter()
     train = W.config4_training()
     gen = R.Rewl([R.instance(**d) for d in train], stream=stream)
-    ok = gen.run_to_convergence(exchange_interval, 5_000_000, poll_cycles=poll_cycles)
+    ok = _converge(gen, exchange_interval, poll_cycles, cap_s, "training runs")
     t_gen = time.perf_counter() - t0
     X, T = WS.training_set(gen, train)
     gen.close()
@@ -333,7 +348,7 @@ def warm_start_workload(seeds=4, exchange_interval=1000, poll_cycles=5):
                 for k in range(seeds):
                     ctx.warm_start(k, net, 2.0 ** -4)
             ts = time.perf_counter()
-            conv = ctx.run_to_convergence(exchange_interval, 20_000_000, poll_cycles=poll_cycles)
+            conv = _converge(ctx, exchange_interval, poll_cycles, cap_s, f"L={L} {mode}")
             torch.cuda.synchronize()
             secs = time.perf_counter() - ts
             sweeps = [int(ctx.counters(k)["conv_sweep"].max()) for k in range(seeds)]
