@@ -98,7 +98,8 @@ rewl_status rewl_create_batch(rewl_ctx **out, const rewl_instance *inst, int n_i
  * ln g(E) += ln f and H(E) += 1 (Sec. II A).  After every `check_every` sweeps
  * (default 1) each walker's flatness is tested; when all m walkers of a window
  * are flat their ln g are averaged, H is reset and ln f halves, or the window
- * converges once ln f <= ln_f_final and then keeps walking with ln g frozen. */
+ * converges once ln f <= ln_f_final and then keeps walking (and exchanging)
+ * with ln g frozen and H no longer counted. */
 rewl_status rewl_run(rewl_ctx *ctx, long n_sweeps);
 
 /* One replica-exchange phase (Eq. (1), Fig. 2): window pairs (i, i+1) with
@@ -146,7 +147,9 @@ rewl_status rewl_geometry(rewl_ctx *ctx, int inst, int *h, int *m, int *B, int *
 /* Full walker state of instance `inst` for inspection and parity tests.  Any
  * pointer may be NULL.  spins: [h*m][N] int8 (Ising +-1, Potts 0..q-1) of the
  * configuration each walker slot holds; E, bin: [h*m]; ln_g: [h*m][w] FP64;
- * H: [h*m][w] (uint32, counts modulo 2^32); stage, conv: [h]; latch: [h*m];
+ * H: [h*m][w] (uint32, counts modulo 2^32); stage, conv: [h] (conv 0 =
+ * running, 1 = converged: ln g frozen and H no longer counted, 2 = sampling
+ * with frozen weights set by rewl_set_initial_lng: H counted); latch: [h*m];
  * replica: [h*m] id of the configuration (follows exchanges). */
 rewl_status rewl_get_state(rewl_ctx *ctx, int inst, int8_t *spins, int64_t *E, int32_t *bin,
                            double *ln_g, uint32_t *H, int32_t *stage, uint8_t *conv,

@@ -40,8 +40,10 @@
  *   - when all m walkers of a window are latched, their ln g are replaced by
  *     the mean, rounded to the nearest multiple of 2^-32 (ties to even);
  *     H is reset; ln f -> ln f / 2, or the window converges if
- *     ln f <= ln_f_final.  Converged windows stop updating ln g, keep
- *     counting H, and keep walking and exchanging.
+ *     ln f <= ln_f_final.  Converged windows stop updating ln g and H
+ *     (the histogram has no role once the window is done) and keep walking
+ *     and exchanging (Sec. II A).  Sampling with given, frozen weights
+ *     (oracle_set_lng with stage0 < 0) does count H.
  *   - random numbers: Philox4x32-10 (Salmon et al., SC'11), key =
  *     (seed_lo, seed_hi ^ instance), counter = (draw_lo, draw_hi,
  *     window << 16 | walker, stream); stream 0 = sweep, 1 = init,
@@ -156,7 +158,9 @@ typedef struct {
     uint64_t *draw;           /* sweep-stream Philox block counter           */
     unsigned char *latch;     /* walker has been flat in the current stage   */
     int *stage;               /* per window: ln f = 2^-stage                 */
-    unsigned char *conv;      /* per window: converged (ln g frozen)         */
+    unsigned char *conv;      /* per window: 0 running; 1 converged (ln g
+                                 frozen, H no longer counted); 2 frozen
+                                 sampling from given weights (H counted)      */
     long *conv_sweep;         /* per window: sweep count at convergence      */
     long sweeps;              /* sweeps done by every walker                 */
     uint64_t t_exch;          /* exchange phases done                        */
@@ -381,7 +385,7 @@ int oracle_init(rewl_oracle *o)
 /* one Wang-Landau trial (Sec. II A): propose, accept with                  */
 /* min(1, g(E)/g(E')), then ln g(E_now) += ln f and H(E_now) += 1.          */
 /* ------------------------------------------------------------------------ */
-static void wl_trial(rewl_oracle *o, int k, int site, int nv, uint32_t r_u, double ln_f, int frozen)
+static void wl_trial(rewl_oracle *o, int k, int site, int nv, uint32_t r_u, double ln_f, int conv)
 {
     int win = k / o->m, lo = o->lo[win];
     signed char *s = o->spin[k];
@@ -401,11 +405,11 @@ static void wl_trial(rewl_oracle *o, int k, int site, int nv, uint32_t r_u, doub
         o->bin[k] = energy_to_bin(o, En);
         o->n_acc[k] += 1;
     }
-    if (!frozen) {
+    if (!conv) {
         lng[o->bin[k] - lo] += ln_f;
         check_exact(o, lng[o->bin[k] - lo]);
     }
-    H[o->bin[k] - lo] += 1;
+    if (conv != 1) H[o->bin[k] - lo] += 1;      /* no histogram after convergence */
 }
 
 /* one sweep = N trials (Sec. IV A: one MC sweep equals N MC steps) */
@@ -413,7 +417,7 @@ static void walker_sweep(rewl_oracle *o, int k)
 {
     int win = k / o->m, j = k % o->m, N = o->N;
     double ln_f = ldexp(1.0, -o->stage[win]);
-    int frozen = o->conv[win];
+    int conv = o->conv[win];
     uint32_t ctr[4] = {0, 0, ((uint32_t)win << 16) | (uint32_t)j, 0};
     int per_block = (o->model == OR_ISING) ? 2 : 1;
     for (int t = 0; t < N; t += per_block) {
@@ -424,12 +428,12 @@ static void walker_sweep(rewl_oracle *o, int k)
         if (o->model == OR_ISING) {
             for (int a = 0; a < 2; ++a) {
                 int site = (int)scale_u32(r[2 * a], (uint32_t)N);
-                wl_trial(o, k, site, -o->spin[k][site], r[2 * a + 1], ln_f, frozen);
+                wl_trial(o, k, site, -o->spin[k][site], r[2 * a + 1], ln_f, conv);
             }
         } else {
             int site = (int)scale_u32(r[0], (uint32_t)N);
             int nv = (o->spin[k][site] + 1 + (int)scale_u32(r[1], (uint32_t)(o->q - 1))) % o->q;
-            wl_trial(o, k, site, nv, r[2], ln_f, frozen);
+            wl_trial(o, k, site, nv, r[2], ln_f, conv);
         }
     }
 }
@@ -574,7 +578,7 @@ int oracle_set_lng(rewl_oracle *o, const double *ln_g_global, int stage0)
                 lng[b] = v;
             }
         }
-        if (stage0 < 0) { o->conv[win] = 1; o->stage[win] = 0; }
+        if (stage0 < 0) { o->conv[win] = 2; o->stage[win] = 0; }
         else { o->conv[win] = 0; o->stage[win] = stage0; }
     }
     return 0;

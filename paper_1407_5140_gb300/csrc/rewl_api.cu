@@ -901,7 +901,7 @@ extern "C" rewl_status rewl_set_initial_lng(rewl_ctx *ctx, int inst, const doubl
     CK(cudaMemset(ctx->d_H + I.lng_off, 0, 4 * u.size()));
     CK(cudaMemset(ctx->d_latch + I.slot0, 0, (size_t)I.h * I.m));
     std::vector<int32_t> st(I.h, k0 < 0 ? 0 : k0);
-    std::vector<uint8_t> cv(I.h, k0 < 0 ? 1 : 0);
+    std::vector<uint8_t> cv(I.h, k0 < 0 ? 2 : 0);     // 2: sampling with frozen weights, H counted
     CK(cudaMemcpy(ctx->d_stage + I.win0, st.data(), 4 * I.h, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_conv + I.win0, cv.data(), I.h, cudaMemcpyHostToDevice));
     return REWL_OK;

@@ -323,7 +323,8 @@ enum : int { kBarFull = 1, kBarEmpty = 3 };  // ids 1, 2 (full) and 3, 4 (empty)
 // (marked by the producers) ends the unrolled loop; lanes whose previous
 // trial moved read its values again there.  H needs no per-trial work while
 // ln f > 0 (it is read off ln g and its value at the stage start); converged
-// windows count it in global memory with fire-and-forget reductions.
+// windows no longer count it, and sampling with frozen weights counts it in
+// global memory with fire-and-forget reductions.
 template <int MODEL>
 __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkItem *items, SweepArgs args)
 {
@@ -453,7 +454,10 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
             }
         } else {
             // ---------------- consumer ----------------
+            // window state: 0 running; 1 converged (ln g frozen, no histogram);
+            // 2 sampling with frozen weights (ln g frozen, H counted)
             const bool frozen = wconv_s[wl_c] != 0;
+            const bool counting = wconv_s[wl_c] == 2;
             const long long lnf = frozen ? 0 : (1LL << (32 - wstage_s[wl_c]));
             long long cur = lng[b];
             uint32_t acc_count = 0;
@@ -461,7 +465,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
             // shared address of ln g of global bin 0 of this walker (bins lo..hi valid)
             const uint32_t lng_sa = (uint32_t)__cvta_generic_to_shared(lng_s + (size_t)tv * wg + kGuard) - 8u * (uint32_t)lo;
             // the rounds of one sweep; kCountH adds the H counting of
-            // converged windows, compiled out where the warp has none: a run
+            // frozen-weight sampling, compiled out where the warp has none: a run
             // of trials that end in the same bin is added to H when the walker
             // leaves the bin (and at the end of the sweep), one trial later
             uint32_t run = 0, prun = 0;
@@ -528,7 +532,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                         if (MODEL == kIsing) sv_next ^= (acc && t1.a_s == t.a_s) ? t.mx : 0u;
                         if (kCountH) {
                             const bool leave = acc && db != 0;
-                            pend = valid && frozen && leave;
+                            pend = valid && counting && leave;
                             Hpend = H + b;
                             prun = run;
                             run = leave ? 1u : run + 1u;
@@ -555,10 +559,10 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                     if (k + 2 < rounds) named_arrive(kBarEmpty + slot, nthreads);
                 }
             };
-            if (__any_sync(0xffffffffu, valid && frozen)) sweep_rounds(std::true_type{});
+            if (__any_sync(0xffffffffu, valid && counting)) sweep_rounds(std::true_type{});
             else sweep_rounds(std::false_type{});
             red_add_global_u32_if(pend, Hpend, prun);
-            red_add_global_u32_if(valid && frozen && run != 0u, H + b, run);
+            red_add_global_u32_if(valid && counting && run != 0u, H + b, run);
             n_acc += acc_count;
         }
         __syncthreads();

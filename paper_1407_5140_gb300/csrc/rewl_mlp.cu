@@ -295,7 +295,7 @@ __global__ void install_kernel(DevState st, int inst, const float *s_pred, int k
     if (threadIdx.x == 0) {
         for (int j = 0; j < I.m; ++j) st.latch[I.slot0 + i * I.m + j] = 0;
         st.stage[gwin] = k0 < 0 ? 0 : k0;
-        st.conv[gwin] = k0 < 0 ? 1 : 0;
+        st.conv[gwin] = k0 < 0 ? 2 : 0;          // 2: sampling with frozen weights
     }
 }
 
