@@ -184,6 +184,37 @@ def test_zhou_bhatt_full_convergence_bit_exact():
     assert cc.mean_relative_error(lg, _golden_lng(8, 65)) < 0.06
 
 
+EXTREMES = [
+    ("ising_L128_h64_m1", _ising(128, 64, 1, seed=41), 2, 2),          # largest lattice, 4 words per row
+    ("potts_q10_L128_h16_m1", _potts(128, 10, 16, 1, seed=42), 1, 2),  # 16 KB lattice, w = 6899
+    ("potts_q127_L8_h2_m2", _potts(8, 127, 2, 2, seed=43), 40, 2),     # largest q
+    ("ising_L8_h1_m32", _ising(8, 1, 32, seed=44), 30, 2),             # a full consumer warp, one window
+    ("ising_L16_h40_o0.9", _ising(16, 40, 2, seed=45, overlap=0.9), 20, 2),   # many narrow windows
+    ("ising_L8_h4_o0", _ising(8, 4, 2, seed=46, overlap=0.0), 40, 3),  # disjoint windows
+    ("ising_L10_h3_m3", _ising(10, 3, 3, seed=47), 40, 2),             # ragged rounds (N = 100)
+]
+
+
+@pytest.mark.parametrize("name,d,sweeps,cycles", EXTREMES, ids=[c[0] for c in EXTREMES])
+def test_extreme_sizes_match_oracle(name, d, sweeps, cycles):
+    """Maximum lattice size, q, walkers per window and window count, disjoint
+    windows and ragged rounds: bit-exact against the oracle."""
+    gpu = make_gpu([d])
+    orc = make_oracle(d)
+    orc.init()
+    assert_same_state(gpu, 0, orc, f"{name} after init")
+    for c in range(cycles):
+        step_both(gpu, [orc], sweeps)
+        assert_same_state(gpu, 0, orc, f"{name} cycle {c}")
+
+
+def test_empty_batch_is_rejected():
+    from paper_1407_5140_gb300 import rewl as R
+    with pytest.raises(R.RewlError) as ei:
+        R.Rewl([])
+    assert ei.value.code == -1
+
+
 def test_graph_cycles_equal_stepwise_calls():
     d = _ising(16, 4, 2, seed=21)
     a = make_gpu([d])
