@@ -379,6 +379,61 @@ def warm_start_workload(seeds=4, exchange_interval=1000, poll_cycles=5, cap_s=90
     print(json.dumps(out))
 
 
+def potts_tc_workload(exchange_interval=1000, poll_cycles=5, cap_s=1500.0):
+    """q = 10 Potts transition temperature from the specific-heat maxima of
+    L = 16..64 lattices (Sec. IV A), all sizes and seeds in one batch run to
+    ln f = 2^-20; per size the peak temperature of every seed, its bootstrap
+    error over the seeds, and the extrapolation Tc(L) = Tc + a / L^2 against
+    the exact 1 / ln(1 + sqrt q)."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1407_5140_gb300 import rewl as R
+    from paper_1407_5140_gb300 import thermo as TH
+    from paper_1407_5140_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ds = W.potts_fss()
+    ctx = R.Rewl([R.instance(**d) for d in ds], stream=stream)
+    ctx.run(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    conv = _converge(ctx, exchange_interval, poll_cycles, cap_s, "potts fss")
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    q = ds[0]["q"]
+    tc_exact = 1.0 / math.log(1.0 + math.sqrt(q))
+    sizes = sorted({d["L"] for d in ds})
+    per = []
+    for L in sizes:
+        ks = [k for k, d in enumerate(ds) if d["L"] == L]
+        peaks, heights, sweeps, lsum = [], [], [], []
+        for k in ks:
+            lg, e = ctx.get_dos(k)
+            t, c = TH.cv_peak(lg, e, 0.6, 0.85)
+            peaks.append(t)
+            heights.append(c / (L * L))
+            sweeps.append(int(ctx.counters(k)["conv_sweep"].max()))
+            lsum.append(_log_sum(lg) - L * L * math.log(q))
+        m, se = TH.bootstrap(np.array(peaks), n_resamples=200, seed=L)
+        per.append({"L": L, "windows": ds[ks[0]]["n_windows"], "T_peak": peaks, "T_peak_mean": m,
+                    "T_peak_bootstrap_err": se, "C_max_per_site": heights, "sweeps_slowest_window": sweeps,
+                    "log_sum_minus_N_ln_q": lsum})
+    Ls = [p["L"] for p in per]
+    tcs = [p["T_peak_mean"] for p in per]
+    errs = [max(p["T_peak_bootstrap_err"], 1e-6) for p in per]
+    tc_inf, tc_err, a = TH.extrapolate_tc(Ls, tcs, errs)
+    tc_inf3, tc_err3, a3 = TH.extrapolate_tc(Ls[2:], tcs[2:], errs[2:])
+    out = {"metric": "q=10 Potts transition temperature from C_v maxima", "n_gpus": 1, "data": "synthetic",
+           "converged": bool(conv), "seconds": secs, "seeds_per_size": len(ds) // len(sizes),
+           "sizes": per, "Tc_inf_fit_all": tc_inf, "Tc_inf_fit_all_err": tc_err, "fit_all_a": a,
+           "Tc_inf_fit_L_ge_32": tc_inf3, "Tc_inf_fit_L_ge_32_err": tc_err3, "Tc_exact": tc_exact}
+    ctx.close()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -388,14 +443,18 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--profile-case", action="store_true",
                     help="only the workload's launch shape with 20 sweeps per launch (for ncu captures)")
-    ap.add_argument("--workload", default="throughput", choices=["throughput", "warm-start"],
-                    help="warm-start: time to converge, learned vs plain (Ising L=128, Potts q=10 L=64)")
+    ap.add_argument("--workload", default="throughput", choices=["throughput", "warm-start", "potts-tc"],
+                    help="warm-start: time to converge, learned vs plain (Ising L=128, Potts q=10 L=64); "
+                         "potts-tc: q=10 Potts transition from C_v maxima, L=16..64")
     args = ap.parse_args()
     if args.profile_case:
         profile_case()
         return
     if args.workload == "warm-start":
         warm_start_workload()
+        return
+    if args.workload == "potts-tc":
+        potts_tc_workload()
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -1,0 +1,92 @@
+"""Thermodynamics from a DOS (paper_1407_5140_gb300/thermo.py) against
+independent routes: Kaufman's exact ln Z(K) differentiated in multiprecision,
+the Potts q = 2 / Ising mapping, and synthetic data with known answers."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import exact_dos as ed
+from paper_1407_5140_gb300 import thermo as TH
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(L):
+    rows = np.loadtxt(os.path.join(GOLDEN, f"ising_L{L}_exact_lng.txt"), usecols=(0, 1))
+    return rows[:, 1], rows[:, 0]
+
+
+def _kaufman_cu(L, T):
+    """Exact U and C of the L x L Ising model at temperature T from
+    d/dK and d^2/dK^2 of ln Z(K) = ln P(K) + 2NK (K = 1/T), multiprecision."""
+    import mpmath
+    N = L * L
+    with mpmath.workdps(60 + N):
+        def lnz(K):
+            return mpmath.log(ed.kaufman_polynomial_value(L, K, mpmath.mp).real) + 2 * N * K
+        K = mpmath.mpf(1) / T
+        d1 = mpmath.diff(lnz, K, 1)
+        d2 = mpmath.diff(lnz, K, 2)
+        return float(-d1), float(K * K * d2)
+
+
+@pytest.mark.parametrize("L", [16, 32])
+def test_canonical_matches_kaufman_derivatives(L):
+    lg, E = _golden(L)
+    Ts = [1.5, 2.0, 2.269, 2.4, 3.5]
+    u, c = TH.canonical(lg, E, Ts)
+    for T, uu, cc in zip(Ts, u, c):
+        ue, ce = _kaufman_cu(L, T)
+        assert abs(uu - ue) <= 1e-9 * L * L, (T, uu, ue)
+        assert abs(cc - ce) <= 1e-8 * ce, (T, cc, ce)
+
+
+def test_limits_and_log_z():
+    lg, E = _golden(16)
+    N = 256
+    u, c = TH.canonical(lg, E, [1e6, 0.05])
+    assert abs(u[0]) < 1e-2 and abs(u[1] + 2 * N) < 1e-6
+    # ln Z at infinite temperature is ln sum g = N ln 2
+    assert abs(TH.log_z(lg, E, 1e12)[0] - N * math.log(2)) < 1e-6
+
+
+def test_cv_peak_against_kaufman_and_known_shift():
+    """The L = 16 peak from the exact DOS sits where the exact C(T) is flat, and
+    above the infinite-lattice T_c = 2 / ln(1 + sqrt 2) by the known O(1/L)
+    finite-size shift."""
+    lg, E = _golden(16)
+    t, cmax = TH.cv_peak(lg, E, 2.0, 2.6)
+    ce = [_kaufman_cu(16, t + dt)[1] for dt in (-1e-4, 0.0, 1e-4)]
+    assert ce[1] >= ce[0] and ce[1] >= ce[2]
+    assert abs(cmax - ce[1]) <= 1e-8 * ce[1]
+    tc = 2.0 / math.log(1.0 + math.sqrt(2.0))
+    assert 0.0 < t - tc < 0.1
+
+
+def test_potts_q2_peak_is_half_the_ising_peak():
+    """E_Ising = 2 E_Potts + 2N for q = 2, so the Potts specific heat is the Ising
+    one at T_Ising = 2 T_Potts, with the same height (exact DOS, L = 6)."""
+    L, N = 6, 36
+    gi = ed.ising_transfer(L)
+    gp = ed.potts_transfer(2, L)
+    ti, ci = TH.cv_peak(np.log(list(gi.values())), np.array(list(gi.keys()), float), 1.5, 3.5)
+    tp, cp = TH.cv_peak(np.log(list(gp.values())), np.array(list(gp.keys()), float), 0.75, 1.75)
+    assert abs(2 * tp - ti) < 1e-8 and abs(cp - ci) < 1e-8 * ci
+
+
+def test_bootstrap_standard_error_of_the_mean():
+    x = np.random.default_rng(5).normal(0.0, 1.0, 64)
+    m, se = TH.bootstrap(x, n_resamples=2000, seed=1)
+    assert m == pytest.approx(x.mean())
+    assert se == pytest.approx(x.std(ddof=1) / 8.0, rel=0.12)
+
+
+def test_extrapolation_recovers_a_known_limit():
+    L = np.array([16, 24, 32, 48, 64])
+    tc, se, a = TH.extrapolate_tc(L, 0.7012316 + 0.83 / L ** 2)
+    assert abs(tc - 0.7012316) < 1e-12 and abs(a - 0.83) < 1e-9
+    tc, se, a = TH.extrapolate_tc(L, 0.7012316 + 0.83 / L ** 2 + np.array([1, -1, 1, -1, 1]) * 1e-4,
+                                  err=np.full(5, 1e-4))
+    assert abs(tc - 0.7012316) < 3 * se and 0.0 < se < 1e-3
