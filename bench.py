@@ -30,10 +30,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 SWEEPS_PER_STEP = 10_000
-# Algorithmic thread-instructions of one single-spin trial (derivation in
-# the design doc): Philox4x32-10 share, site and neighbour indices, the -ln u
-# threshold, neighbour reads and the energy change, the ln g lookup and
-# comparison, the accepted move, and the ln g / H updates.
+# Algorithmic thread-instructions of one single-spin trial, counted from the
+# minimal operation sequence: Philox4x32-10 share 30 (Ising, two trials per
+# block) / 60 (Potts), site and neighbour indices 11, the -ln u threshold 35,
+# neighbour reads and the energy change 20, the ln g lookup and comparison 8,
+# the accepted move and the ln g / H updates 6.
 INSTR_PER_TRIAL = {0: 110, 1: 146}
 N_SM = 152
 MAX_SM_MHZ = 2070.0
@@ -434,6 +435,55 @@ def potts_tc_workload(exchange_interval=1000, poll_cycles=5, cap_s=1500.0):
     print(json.dumps(out))
 
 
+def exchange_study_workload(intervals=(100, 1000, 10000, 0), cap_s=600.0):
+    """Algorithmic effect of the replica-exchange frequency (Sec. IV B): MC
+    sweeps of the slowest window to finish the first WL iteration and the first
+    eight, q = 10 Potts 48 x 48 with 15 windows and one walker each, for
+    exchanges every X sweeps (X = 0: no exchange).  Per-window sweep counts at
+    convergence are exact (no polling error)."""
+    import numpy as np
+    import torch
+    from paper_1407_5140_gb300 import rewl as R
+    from paper_1407_5140_gb300 import thermo as TH
+    from paper_1407_5140_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ds = W.exchange_study()
+    res = []
+    for X in intervals:
+        ctx = R.Rewl([R.instance(**d) for d in ds], stream=stream)
+        t0 = time.perf_counter()
+        step = X if X else 1000
+        done = False
+        while not done and time.perf_counter() - t0 < cap_s:
+            for _ in range(20):
+                if X:
+                    ctx.run_cycles(1, X)
+                else:
+                    ctx.run(step)
+            done = ctx.status(0)["all_converged"]
+        secs = time.perf_counter() - t0
+        first = [int(ctx.counters(k)["conv_sweep"].max()) for k, d in enumerate(ds) if d["ln_f_final"] == 1.0]
+        eight = [int(ctx.counters(k)["conv_sweep"].max()) for k, d in enumerate(ds) if d["ln_f_final"] < 1.0]
+        ex = ctx.counters(0)
+        alpha = float(ex["ex_acc"].sum()) / max(1.0, float(ex["ex_prop"].sum()))
+        m1, e1 = TH.bootstrap(np.array(first, float), seed=1)
+        m8, e8 = TH.bootstrap(np.array(eight, float), seed=8)
+        res.append({"exchange_every": X or None, "converged": bool(done), "seconds": secs,
+                    "sweeps_first_iteration": first, "mean_first": m1, "err_first": e1,
+                    "sweeps_eight_iterations": eight, "mean_eight": m8, "err_eight": e8,
+                    "exchange_acceptance": alpha})
+        ctx.close()
+    base = [r for r in res if r["exchange_every"] is None][0]
+    for r in res:
+        r["speedup_first"] = base["mean_first"] / r["mean_first"]
+        r["speedup_eight"] = base["mean_eight"] / r["mean_eight"]
+    print(json.dumps({"metric": "algorithmic speedup from replica exchange", "n_gpus": 1, "data": "synthetic",
+                      "workload": "q=10 Potts 48x48, 15 windows at 75%, m=1, 8 seeds", "results": res}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -443,9 +493,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--profile-case", action="store_true",
                     help="only the workload's launch shape with 20 sweeps per launch (for ncu captures)")
-    ap.add_argument("--workload", default="throughput", choices=["throughput", "warm-start", "potts-tc"],
+    ap.add_argument("--workload", default="throughput", choices=["throughput", "warm-start", "potts-tc", "exchange"],
                     help="warm-start: time to converge, learned vs plain (Ising L=128, Potts q=10 L=64); "
-                         "potts-tc: q=10 Potts transition from C_v maxima, L=16..64")
+                         "potts-tc: q=10 Potts transition from C_v maxima, L=16..64; "
+                         "exchange: sweeps to finish WL iterations vs exchange frequency")
     args = ap.parse_args()
     if args.profile_case:
         profile_case()
@@ -455,6 +506,9 @@ def main():
         return
     if args.workload == "potts-tc":
         potts_tc_workload()
+        return
+    if args.workload == "exchange":
+        exchange_study_workload()
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

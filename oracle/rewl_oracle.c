@@ -19,7 +19,7 @@
  *     run-past-convergence:                       Sec. II A
  *   - Potts Hamiltonian, single-spin update:      Sec. III A, Eq. (2)
  *
- * Readings where the paper is silent (each one is listed in the design doc):
+ * Readings where the paper is silent:
  *   - ln g is FP64; every value it takes is a multiple of 2^-32 below 2^21
  *     in magnitude, so differences are exact.  The oracle checks the bound.
  *   - accept iff (ln g(E') - ln g(E)) * 2^32 < lam_fix, where

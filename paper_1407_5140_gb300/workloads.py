@@ -83,6 +83,18 @@ def potts_fss(sizes=(16, 24, 32, 48, 64), seeds=4, q=10, width=490):
     return out
 
 
+def exchange_study(seeds=8, L=48, q=10, h=15):
+    """q-state Potts L x L with h windows at 75 % overlap and one walker per
+    window, run through the first WL iteration (ln f_final = 1) and through
+    the first eight (ln f_final = 2^-7): the exchange-frequency experiment of
+    Sec. IV B."""
+    out = []
+    for s in range(seeds):
+        out.append(_inst(POTTS, L, q, h, 1, 9000 + s, ln_f_final=1.0))
+        out.append(_inst(POTTS, L, q, h, 1, 9100 + s, ln_f_final=2.0 ** -7))
+    return out
+
+
 def _h(L):
     return int(min(32, max(4, round(L * L / 128))))
 
