@@ -192,6 +192,8 @@ EXTREMES = [
     ("ising_L16_h40_o0.9", _ising(16, 40, 2, seed=45, overlap=0.9), 20, 2),   # many narrow windows
     ("ising_L8_h4_o0", _ising(8, 4, 2, seed=46, overlap=0.0), 40, 3),  # disjoint windows
     ("ising_L10_h3_m3", _ising(10, 3, 3, seed=47), 40, 2),             # ragged rounds (N = 100)
+    ("config4_ising_L128_h64_m4", _ising(128, 64, 4, seed=48), 1, 2),  # warm-start target shapes
+    ("config4_potts_q10_L64_h64_m4", _potts(64, 10, 64, 4, seed=49), 2, 2),
 ]
 
 
@@ -206,6 +208,29 @@ def test_extreme_sizes_match_oracle(name, d, sweeps, cycles):
     for c in range(cycles):
         step_both(gpu, [orc], sweeps)
         assert_same_state(gpu, 0, orc, f"{name} cycle {c}")
+
+
+def test_learned_warm_start_install_then_bit_exact():
+    """rewl_warm_start writes each walker's ln g from the network (window
+    pieces shifted to a zero minimum), resets H and latches and sets the stage;
+    the oracle given the same ln g and stage then follows the GPU bit for bit."""
+    from paper_1407_5140_gb300 import rewl as R
+    d = _ising(16, 4, 2, seed=50)
+    gpu = make_gpu([d])
+    net = R.Mlp(max_batch=1024, seed=3)
+    gpu.warm_start(0, net, 2.0 ** -4)
+    g = gpu.state(0, 256)
+    assert np.all(g["stage"] == 4) and not np.any(g["conv"]) and not np.any(g["H"]) and not np.any(g["latch"])
+    orc = make_oracle(d)
+    orc.init()
+    orc.set_lng(np.zeros(orc.B), 4)
+    for k in range(orc.n_walkers):
+        orc.set_walker_lng(k, g["lng"][k])
+    assert_same_state(gpu, 0, orc, "after the warm start")
+    for c in range(4):
+        step_both(gpu, [orc], 100)
+        assert_same_state(gpu, 0, orc, f"warm start cycle {c}")
+    net.close()
 
 
 def test_empty_batch_is_rejected():
