@@ -47,6 +47,9 @@ def lib():
         L.oracle_all_converged.argtypes = [vp]
         L.oracle_set_check_every.argtypes = [vp, i64]
         L.oracle_set_flat_rule.argtypes = [vp, C.c_int]
+        L.oracle_set_windows.argtypes = [vp, vp, vp]
+        L.oracle_set_windows.restype = C.c_int
+        L.oracle_window_widths.argtypes = [vp, vp]
         L.oracle_zb_flat.argtypes = [C.c_uint64, C.c_double, C.c_int]
         L.oracle_zb_flat.restype = C.c_int
         L.oracle_error.argtypes = [vp]
@@ -97,7 +100,8 @@ class Oracle:
     """One REWL instance: h windows x m walkers on an L x L lattice."""
 
     def __init__(self, model, L, q, e_min, e_max, n_windows, overlap, walkers_per_window,
-                 flatness=0.8, ln_f_final=2.0 ** -20, seed=0, instance=0, threads=0, flat_rule=0):
+                 flatness=0.8, ln_f_final=2.0 ** -20, seed=0, instance=0, threads=0, flat_rule=0,
+                 windows=None):
         self.model, self.L, self.q = model, L, (2 if model == ISING else q)
         self.N = L * L
         self.h, self.m = n_windows, walkers_per_window
@@ -107,6 +111,12 @@ class Oracle:
         if not self._o:
             raise ValueError("oracle_create rejected the parameters")
         lib().oracle_set_flat_rule(self._o, flat_rule)
+        if windows is not None:
+            lo = np.ascontiguousarray(windows[0], dtype=np.int32)
+            hi = np.ascontiguousarray(windows[1], dtype=np.int32)
+            assert lo.size == n_windows and hi.size == n_windows
+            if lib().oracle_set_windows(self._o, _p(lo), _p(hi)):
+                raise ValueError("oracle_set_windows rejected the windows")
         B = np.zeros(1, np.int32)
         w = np.zeros(1, np.int32)
         lib().oracle_geometry(self._o, _p(B), _p(w), None, None)
@@ -114,6 +124,8 @@ class Oracle:
         self.lo = np.zeros(self.h, np.int32)
         self.reach = np.zeros(self.B, np.uint8)
         lib().oracle_geometry(self._o, _p(B), _p(w), _p(self.lo), _p(self.reach))
+        self.ww = np.zeros(self.h, np.int32)             # bins of each window (w: the widest)
+        lib().oracle_window_widths(self._o, _p(self.ww))
         self.step = 4 if model == ISING else 1
         self.e_min, self.e_max = e_min, e_max
 

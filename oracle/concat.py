@@ -27,10 +27,12 @@ def stencil_beta(f, b, s, dE):
 
 
 def concatenate(pieces, lo, w, reach, dE, ln_g_min, s=1):
-    """pieces: (h, w) ln g per window on window-local bins; lo: first global bin
-    of each window; reach: (B,) realisable-energy mask.  Returns (ln_g (B,),
-    joins (h-1,)) with ln_g = nan on unrealisable bins."""
+    """pieces: (h, >= w) ln g per window on window-local bins; lo: first global
+    bin of each window; w: bins per window (one number, or one per window);
+    reach: (B,) realisable-energy mask.  Returns (ln_g (B,), joins (h-1,))
+    with ln_g = nan on unrealisable bins."""
     h = len(pieces)
+    ws = np.broadcast_to(np.asarray(w), (h,))
     B = len(reach)
     glob = np.full(B, np.nan)
     joins = []
@@ -38,7 +40,7 @@ def concatenate(pieces, lo, w, reach, dE, ln_g_min, s=1):
     start = lo[0]                # first bin taken from piece i
     for i in range(h - 1):
         a_lo, b_lo = lo[i], lo[i + 1]
-        ov_lo, ov_hi = max(a_lo, b_lo), min(a_lo + w - 1, b_lo + w - 1)
+        ov_lo, ov_hi = max(a_lo, b_lo), min(a_lo + ws[i] - 1, b_lo + ws[i + 1] - 1)
         fa = lambda b, i=i: pieces[i][b - lo[i]]
         fb = lambda b, i=i: pieces[i + 1][b - lo[i + 1]]
         best, best_d = None, None
@@ -58,7 +60,7 @@ def concatenate(pieces, lo, w, reach, dE, ln_g_min, s=1):
             glob[b] = fa(b) + shift
         shift = fa(best) + shift - fb(best)
         start = best
-    for b in range(start, lo[h - 1] + w):
+    for b in range(start, lo[h - 1] + ws[h - 1]):
         glob[b] = pieces[h - 1][b - lo[h - 1]] + shift
     glob[~reach.astype(bool)] = np.nan
     first = int(np.argmax(reach))

@@ -142,6 +142,8 @@ typedef struct {
     int B;                    /* number of bins in [e_min, e_max]            */
     int h, m, w;              /* windows, walkers per window, bins/window    */
     int *lo;                  /* first global bin of each window             */
+    int *ww;                  /* bins of each window (w is the widest: the
+                                 row length of ln g and H)                    */
     unsigned char *reach;     /* reach[b]: energy of bin b is realisable     */
     int *n_reach;             /* reachable bins in each window               */
     double p_flat, ln_f_final;
@@ -215,7 +217,7 @@ static int bin_in_window(const rewl_oracle *o, int win, long E)
 {
     if (E < o->e_min || E > o->e_max) return 0;
     int b = energy_to_bin(o, E);
-    return b >= o->lo[win] && b <= o->lo[win] + o->w - 1;
+    return b >= o->lo[win] && b <= o->lo[win] + o->ww[win] - 1;
 }
 
 /* Realisable energies on an even L x L periodic lattice (L >= 4):
@@ -287,12 +289,16 @@ rewl_oracle *oracle_create(int model, int L, int q, long e_min, long e_max,
     o->B = (int)((e_max - e_min) / o->step) + 1;
     o->h = h; o->m = m;
     o->lo = (int *)calloc(h, sizeof(int));
+    o->ww = (int *)calloc(h, sizeof(int));
     if (oracle_windows(o->B, h, overlap, o->lo, &o->w)) { oracle_destroy(o); return NULL; }
     o->reach = (unsigned char *)calloc(o->B, 1);
     for (int b = 0; b < o->B; ++b) o->reach[b] = (unsigned char)energy_reachable(o, e_min + (long)b * o->step);
     o->n_reach = (int *)calloc(h, sizeof(int));
     for (int i = 0; i < h; ++i)
+    {
         for (int b = o->lo[i]; b < o->lo[i] + o->w; ++b) o->n_reach[i] += o->reach[b];
+        o->ww[i] = o->w;
+    }
     o->p_flat = p_flat; o->ln_f_final = ln_f_final;
     o->check_every = 1;
     o->key0 = (uint32_t)seed;
@@ -325,7 +331,7 @@ void oracle_destroy(rewl_oracle *o)
     if (o->spin) for (int k = 0; k < o->n_walkers; ++k) free(o->spin[k]);
     free(o->spin); free(o->E); free(o->bin); free(o->replica); free(o->lng); free(o->H);
     free(o->draw); free(o->latch); free(o->stage); free(o->conv); free(o->conv_sweep);
-    free(o->ex_prop); free(o->ex_acc); free(o->n_acc); free(o->lo); free(o->reach);
+    free(o->ex_prop); free(o->ex_acc); free(o->n_acc); free(o->lo); free(o->ww); free(o->reach);
     free(o->n_reach); free(o);
 }
 
@@ -451,7 +457,7 @@ static int walker_flat(const rewl_oracle *o, int k)
     int win = k / o->m, lo = o->lo[win];
     const uint64_t *H = o->H + (size_t)k * o->w;
     uint64_t mn = UINT64_MAX, sum = 0;
-    for (int b = 0; b < o->w; ++b) {
+    for (int b = 0; b < o->ww[win]; ++b) {
         if (!o->reach[lo + b]) continue;
         if (H[b] < mn) mn = H[b];
         sum += H[b];
@@ -482,7 +488,7 @@ static void window_boundary(rewl_oracle *o, int win)
         all &= o->latch[k];
     }
     if (!all) return;
-    for (int b = 0; b < o->w; ++b) {
+    for (int b = 0; b < o->ww[win]; ++b) {
         int64_t units = 0;
         for (int j = 0; j < m; ++j) {
             double v = o->lng[(size_t)(win * m + j) * o->w + b];
@@ -572,7 +578,7 @@ int oracle_set_lng(rewl_oracle *o, const double *ln_g_global, int stage0)
     for (int win = 0; win < o->h; ++win) {
         for (int j = 0; j < o->m; ++j) {
             double *lng = o->lng + (size_t)(win * o->m + j) * o->w;
-            for (int b = 0; b < o->w; ++b) {
+            for (int b = 0; b < o->ww[win]; ++b) {
                 double v = nearbyint(ln_g_global[o->lo[win] + b] * 4294967296.0) / 4294967296.0;
                 if (!check_exact(o, v)) return o->error;
                 lng[b] = v;
@@ -604,6 +610,36 @@ void oracle_geometry(const rewl_oracle *o, int *B, int *w, int *lo, unsigned cha
     if (lo) memcpy(lo, o->lo, sizeof(int) * o->h);
     if (reach) memcpy(reach, o->reach, o->B);
 }
+
+/* Windows of any widths (the run-time-balanced windows of Sec. V): window i
+ * covers bins lo[i]..hi[i].  They must start at bin 0, end at bin B-1, have
+ * increasing lower and upper ends and overlap their neighbour by at least one
+ * bin.  Call before oracle_init.  Returns 0, or -1 for an invalid set. */
+int oracle_set_windows(rewl_oracle *o, const int *lo, const int *hi)
+{
+    int h = o->h, wmax = 0;
+    if (lo[0] != 0 || hi[h - 1] != o->B - 1) return -1;
+    for (int i = 0; i < h; ++i) {
+        if (hi[i] < lo[i] || hi[i] >= o->B) return -1;
+        if (i + 1 < h && (lo[i + 1] <= lo[i] || hi[i + 1] <= hi[i] || lo[i + 1] > hi[i])) return -1;
+        if (hi[i] - lo[i] + 1 > wmax) wmax = hi[i] - lo[i] + 1;
+    }
+    if (wmax != o->w) {
+        free(o->lng); free(o->H);
+        o->w = wmax;
+        o->lng = (double *)calloc((size_t)o->n_walkers * o->w, sizeof(double));
+        o->H = (uint64_t *)calloc((size_t)o->n_walkers * o->w, sizeof(uint64_t));
+    }
+    for (int i = 0; i < h; ++i) {
+        o->lo[i] = lo[i];
+        o->ww[i] = hi[i] - lo[i] + 1;
+        o->n_reach[i] = 0;
+        for (int b = lo[i]; b <= hi[i]; ++b) o->n_reach[i] += o->reach[b];
+    }
+    return 0;
+}
+
+void oracle_window_widths(const rewl_oracle *o, int *ww) { memcpy(ww, o->ww, sizeof(int) * (size_t)o->h); }
 
 /* spins_out: [n_walkers][N] as stored (Ising +-1, Potts 0..q-1) */
 void oracle_get_state(const rewl_oracle *o, signed char *spins_out, long *E_out, int *bin_out,

@@ -377,6 +377,47 @@ def test_concatenate_reassembles_exact_pieces():
     assert np.all(np.diff(joins) > 0)
 
 
+UNEVEN_LO, UNEVEN_HI = [0, 14, 30, 44], [24, 38, 52, 64]     # Ising L = 8, B = 65: widths 25, 25, 23, 21
+
+
+def test_uneven_windows_rejected_when_invalid():
+    bad = [([1, 14, 30, 44], [24, 38, 52, 64]),     # does not start at bin 0
+           ([0, 14, 30, 44], [24, 38, 52, 63]),     # does not end at bin B - 1
+           ([0, 25, 30, 44], [24, 38, 52, 64]),     # gap between windows 0 and 1
+           ([0, 14, 14, 44], [24, 38, 52, 64]),     # lower ends not increasing
+           ([0, 14, 30, 44], [24, 38, 38, 64])]     # upper ends not increasing
+    for lo, hi in bad:
+        with pytest.raises(ValueError):
+            O.Oracle(0, 8, 2, -128, 128, 4, 0.75, 1, windows=(lo, hi))
+
+
+def test_concatenate_reassembles_uneven_pieces():
+    L, B = 8, 65
+    ex = _exact_ising_lng(L, B)
+    reach = np.isfinite(ex).astype(np.uint8)
+    ww = np.array(UNEVEN_HI) - np.array(UNEVEN_LO) + 1
+    pieces = np.zeros((4, ww.max()))
+    for i, (l, n) in enumerate(zip(UNEVEN_LO, ww)):
+        pieces[i, :n] = np.nan_to_num(ex[l:l + n]) - 5.0 * i
+    lg, joins = cc.concatenate(pieces, UNEVEN_LO, ww, reach, 4.0, math.log(2))
+    assert np.allclose(lg[reach.astype(bool)], ex[reach.astype(bool)], atol=1e-9)
+
+
+def test_wl_with_uneven_windows_converges():
+    """Windows of different widths (Sec. V: run-time-balanced windows) change
+    nothing in the method; the joined DOS converges to the exact one."""
+    ex = _exact_ising_lng(8, 65)
+    eps = []
+    for seed in range(4):
+        o = O.Oracle(0, 8, 2, -128, 128, 4, 0.75, 2, seed=seed, windows=(UNEVEN_LO, UNEVEN_HI))
+        assert list(o.lo) == UNEVEN_LO and list(o.ww) == [25, 25, 23, 21] and o.w == 25
+        o.init()
+        assert o.run_to_convergence(1000, 3_000_000)
+        lg, _ = cc.concatenate(o.pieces(), o.lo, o.ww, o.reach, 4.0, math.log(2))
+        eps.append(cc.mean_relative_error(lg, ex))
+    assert np.mean(eps) < 0.02, eps
+
+
 # ---------------------------------------------------------------------------
 # warm-start network reference: chain-rule gradient against finite differences
 # ---------------------------------------------------------------------------
