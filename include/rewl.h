@@ -93,6 +93,19 @@ rewl_status rewl_create(rewl_ctx **out, rewl_model model, int L, int q,
 rewl_status rewl_create_batch(rewl_ctx **out, const rewl_instance *inst, int n_inst,
                               void *cuda_stream);
 
+/* As rewl_create_batch, with every window given bin by bin instead of by the
+ * equal-width rule: windows of different widths, e.g. sized so that they
+ * finish their WL iterations at a similar pace (the run-time-balanced windows
+ * of Sec. V).  lo, hi: host arrays of sum(inst[k].n_windows) bin indices,
+ * instance after instance; window i of an instance covers bins lo[i]..hi[i]
+ * (inclusive).  Per instance the windows must start at bin 0, end at bin
+ * B - 1, have increasing lower and upper ends, overlap their neighbour by at
+ * least one bin and be at least 2 * (largest bin change) + 1 bins wide (5
+ * Ising, 9 Potts); otherwise REWL_EINVAL.  The instance's `overlap` field is
+ * not used.  Read during the call. */
+rewl_status rewl_create_batch_windows(rewl_ctx **out, const rewl_instance *inst, int n_inst,
+                                      const int32_t *lo, const int32_t *hi, void *cuda_stream);
+
 /* n_sweeps Wang-Landau sweeps of every walker (one sweep = N single-spin
  * trials, Sec. IV A), each trial accepted with min(1, g(E)/g(E')), followed by
  * ln g(E) += ln f and H(E) += 1 (Sec. II A).  After every `check_every` sweeps
@@ -118,7 +131,8 @@ rewl_status rewl_run_to_convergence(rewl_ctx *ctx, long exchange_interval, long 
                                     long poll_cycles, int *converged);
 
 /* ln g of instance `inst`.  per_window = 1: the h pieces, h*w values, each the
- * walker mean of its window (identical after a merge).  per_window = 0: the
+ * walker mean of its window (identical after a merge; NaN past the end of a
+ * window narrower than w).  per_window = 0: the
  * pieces joined as in Sec. II B (five-point inverse-temperature estimate,
  * join where the pieces' estimates agree best) and normalised so that
  * ln g(e_min) = ln 2 (Ising) or ln q (Potts); B values, NaN on energies no
@@ -139,10 +153,15 @@ rewl_status rewl_status_query(rewl_ctx *ctx, int inst, int *all_converged, doubl
 rewl_status rewl_set_initial_lng(rewl_ctx *ctx, int inst, const double *ln_g0, double ln_f_start);
 
 /* Geometry of instance `inst` (any pointer may be NULL): windows h, walkers
- * per window m, bins B, window width w, lo[h] = first bin of each window,
- * reach[B] (1 = some configuration has that energy). */
+ * per window m, bins B, window width w (the widest window: the length of each
+ * walker's ln g and H rows), lo[h] = first bin of each window, reach[B] (1 =
+ * some configuration has that energy). */
 rewl_status rewl_geometry(rewl_ctx *ctx, int inst, int *h, int *m, int *B, int *w, int *lo,
                           uint8_t *reach);
+
+/* Bins of each window of instance `inst` (ww[h]; all equal to w unless the
+ * windows were given to rewl_create_batch_windows). */
+rewl_status rewl_window_widths(rewl_ctx *ctx, int inst, int32_t *ww);
 
 /* Full walker state of instance `inst` for inspection and parity tests.  Any
  * pointer may be NULL.  spins: [h*m][N] int8 (Ising +-1, Potts 0..q-1) of the

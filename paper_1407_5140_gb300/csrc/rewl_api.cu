@@ -25,6 +25,7 @@ struct HostInst {
     rewl_instance desc;
     InstDev dev;
     std::vector<int> lo;
+    std::vector<int> ww;          // bins of each window (dev.w is the widest)
     std::vector<uint8_t> reach;
     std::vector<int> n_reach;
 };
@@ -45,7 +46,7 @@ struct rewl_ctx {
     long long n_lng = 0, n_lat = 0, n_reach_bytes = 0;
     // device buffers
     InstDev *d_inst = nullptr;
-    int32_t *d_lo = nullptr, *d_nreach = nullptr, *d_stage = nullptr;
+    int32_t *d_lo = nullptr, *d_ww = nullptr, *d_nreach = nullptr, *d_stage = nullptr;
     uint8_t *d_conv = nullptr;
     int64_t *d_conv_sweep = nullptr;
     ull *d_ex_prop = nullptr, *d_ex_acc = nullptr;
@@ -114,7 +115,8 @@ static bool realisable(int model, int q, long long N, long long E)
     return !(off == 1 || off == 2 || off == 3 || off == 5);
 }
 
-static rewl_status build_instance(const rewl_instance &d, HostInst &hi, std::string &why)
+static rewl_status build_instance(const rewl_instance &d, HostInst &hi, std::string &why,
+                                  const int32_t *clo = nullptr, const int32_t *chi = nullptr)
 {
     char buf[256];
     if (d.model != REWL_ISING && d.model != REWL_POTTS) { why = "model must be REWL_ISING or REWL_POTTS"; return REWL_EINVAL; }
@@ -145,15 +147,33 @@ static rewl_status build_instance(const rewl_instance &d, HostInst &hi, std::str
     int w = (int)std::ceil((double)B / span);
     if (w > B) w = B;
     const int maxdb = d.model == REWL_ISING ? 2 : 4;
-    if (w < 2 * maxdb + 1) { why = "windows narrower than 2 * (largest bin change) + 1"; return REWL_EINVAL; }
+    if (!clo && w < 2 * maxdb + 1) { why = "windows narrower than 2 * (largest bin change) + 1"; return REWL_EINVAL; }
     hi.desc = d;
     hi.lo.resize(h);
+    hi.ww.assign(h, w);
     for (int i = 0; i < h; ++i) hi.lo[i] = h == 1 ? 0 : (int)(((long long)i * (B - w)) / (h - 1));
+    if (clo) {
+        // windows given bin by bin (run-time-balanced windows, Sec. V): from bin 0
+        // to bin B - 1, increasing ends, each overlapping the next
+        if (clo[0] != 0 || chi[h - 1] != B - 1) { why = "windows must start at bin 0 and end at bin B - 1"; return REWL_EINVAL; }
+        w = 0;
+        for (int i = 0; i < h; ++i) {
+            if (chi[i] < clo[i] || chi[i] >= B) { why = "window " + std::to_string(i) + " is empty or past bin B - 1"; return REWL_EINVAL; }
+            if (i + 1 < h && (clo[i + 1] <= clo[i] || chi[i + 1] <= chi[i] || clo[i + 1] > chi[i])) {
+                why = "windows " + std::to_string(i) + " and " + std::to_string(i + 1) + " must overlap with increasing ends";
+                return REWL_EINVAL;
+            }
+            hi.lo[i] = clo[i];
+            hi.ww[i] = chi[i] - clo[i] + 1;
+            if (hi.ww[i] < 2 * maxdb + 1) { why = "windows narrower than 2 * (largest bin change) + 1"; return REWL_EINVAL; }
+            w = std::max(w, hi.ww[i]);
+        }
+    }
     hi.reach.resize(B);
     for (int b = 0; b < B; ++b) hi.reach[b] = realisable(d.model, q, N, d.e_min + (long long)b * step);
     hi.n_reach.assign(h, 0);
     for (int i = 0; i < h; ++i)
-        for (int b = hi.lo[i]; b < hi.lo[i] + w; ++b) hi.n_reach[i] += hi.reach[b];
+        for (int b = hi.lo[i]; b < hi.lo[i] + hi.ww[i]; ++b) hi.n_reach[i] += hi.reach[b];
     for (int i = 0; i < h; ++i)
         if (hi.n_reach[i] == 0) { why = "a window holds no realisable energy"; return REWL_EINVAL; }
     int kf = 0;
@@ -193,15 +213,37 @@ static cudaError_t dalloc(T **p, size_t n)
 extern "C" void rewl_destroy(rewl_ctx *ctx);
 static rewl_status plan(rewl_ctx *ctx);
 
+static rewl_status create_batch(rewl_ctx **out, const rewl_instance *inst, int n_inst, const int32_t *lo,
+                                const int32_t *hi, void *cuda_stream);
+
 extern "C" rewl_status rewl_create_batch(rewl_ctx **out, const rewl_instance *inst, int n_inst, void *cuda_stream)
+{
+    return create_batch(out, inst, n_inst, nullptr, nullptr, cuda_stream);
+}
+
+extern "C" rewl_status rewl_create_batch_windows(rewl_ctx **out, const rewl_instance *inst, int n_inst,
+                                                 const int32_t *lo, const int32_t *hi, void *cuda_stream)
+{
+    if (!lo || !hi) return fail(nullptr, REWL_EINVAL, "rewl_create_batch_windows: lo or hi is NULL");
+    return create_batch(out, inst, n_inst, lo, hi, cuda_stream);
+}
+
+static rewl_status create_batch(rewl_ctx **out, const rewl_instance *inst, int n_inst, const int32_t *lo,
+                                const int32_t *hi, void *cuda_stream)
 {
     if (!out || !inst || n_inst < 1) return fail(nullptr, REWL_EINVAL, "rewl_create_batch: null argument or n_inst < 1");
     *out = nullptr;
     rewl_ctx *ctx = new rewl_ctx();
     ctx->inst.resize(n_inst);
+    long long woff = 0;
     for (int k = 0; k < n_inst; ++k) {
         std::string why;
-        rewl_status s = build_instance(inst[k], ctx->inst[k], why);
+        if (inst[k].n_windows < 1 || inst[k].n_windows > 65535) {
+            delete ctx;
+            return fail(nullptr, REWL_EINVAL, "instance " + std::to_string(k) + ": n_windows must be in 1..65535");
+        }
+        rewl_status s = build_instance(inst[k], ctx->inst[k], why, lo ? lo + woff : nullptr, hi ? hi + woff : nullptr);
+        woff += inst[k].n_windows;
         if (s != REWL_OK) {
             delete ctx;
             return fail(nullptr, s, "instance " + std::to_string(k) + ": " + why);
@@ -210,7 +252,7 @@ extern "C" rewl_status rewl_create_batch(rewl_ctx **out, const rewl_instance *in
     // offsets
     long long lng = 0, lat = 0, rch = 0;
     int win = 0, slot = 0;
-    std::vector<int32_t> lo_all, nreach_all, slot_inst;
+    std::vector<int32_t> lo_all, ww_all, nreach_all, slot_inst;
     std::vector<uint8_t> reach_all;
     std::vector<ExTask> ex0, ex1;
     for (int k = 0; k < n_inst; ++k) {
@@ -229,6 +271,7 @@ extern "C" rewl_status rewl_create_batch(rewl_ctx **out, const rewl_instance *in
         rch += I.B;
         for (int i = 0; i < I.h; ++i) {
             lo_all.push_back(h.lo[i]);
+            ww_all.push_back(h.ww[i]);
             nreach_all.push_back(h.n_reach[i]);
         }
         reach_all.insert(reach_all.end(), h.reach.begin(), h.reach.end());
@@ -255,6 +298,7 @@ extern "C" rewl_status rewl_create_batch(rewl_ctx **out, const rewl_instance *in
     for (auto &h : ctx->inst) idev.push_back(h.dev);
     CK(dalloc(&ctx->d_inst, n_inst));
     CK(dalloc(&ctx->d_lo, win));
+    CK(dalloc(&ctx->d_ww, win));
     CK(dalloc(&ctx->d_nreach, win));
     CK(dalloc(&ctx->d_stage, win));
     CK(dalloc(&ctx->d_conv, win));
@@ -281,6 +325,7 @@ extern "C" rewl_status rewl_create_batch(rewl_ctx **out, const rewl_instance *in
     cudaStream_t s = ctx->stream;
     CK(cudaMemcpyAsync(ctx->d_inst, idev.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->d_lo, lo_all.data(), 4 * win, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_ww, ww_all.data(), 4 * win, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->d_nreach, nreach_all.data(), 4 * win, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->d_reach, reach_all.data(), rch, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->d_slot_inst, slot_inst.data(), 4 * slot, cudaMemcpyHostToDevice, s));
@@ -299,6 +344,7 @@ extern "C" rewl_status rewl_create_batch(rewl_ctx **out, const rewl_instance *in
     DevState &st = ctx->st;
     st.inst = ctx->d_inst;
     st.lo = ctx->d_lo;
+    st.ww = ctx->d_ww;
     st.n_reach = ctx->d_nreach;
     st.stage = ctx->d_stage;
     st.conv = ctx->d_conv;
@@ -361,7 +407,7 @@ extern "C" void rewl_destroy(rewl_ctx *ctx)
         if (c.stream) cudaStreamDestroy(c.stream);
         if (c.done) cudaEventDestroy(c.done);
     }
-    void *bufs[] = {ctx->d_inst, ctx->d_lo, ctx->d_nreach, ctx->d_stage, ctx->d_conv, ctx->d_conv_sweep,
+    void *bufs[] = {ctx->d_inst, ctx->d_lo, ctx->d_ww, ctx->d_nreach, ctx->d_stage, ctx->d_conv, ctx->d_conv_sweep,
                     ctx->d_ex_prop, ctx->d_ex_acc, ctx->d_cfg, ctx->d_E, ctx->d_bin, ctx->d_replica,
                     ctx->d_slot_inst, ctx->d_draw, ctx->d_nacc, ctx->d_latch, ctx->d_lng, ctx->d_lng0, ctx->d_H,
                     ctx->d_lat, ctx->d_reach, ctx->d_counters, ctx->d_error, ctx->d_ex0, ctx->d_ex1};
@@ -672,6 +718,14 @@ extern "C" rewl_status rewl_geometry(rewl_ctx *ctx, int inst, int *hh, int *m, i
     return REWL_OK;
 }
 
+extern "C" rewl_status rewl_window_widths(rewl_ctx *ctx, int inst, int32_t *ww)
+{
+    if (!ctx || !ww || inst < 0 || inst >= (int)ctx->inst.size()) return REWL_EINVAL;
+    const HostInst &h = ctx->inst[inst];
+    std::copy(h.ww.begin(), h.ww.end(), ww);
+    return REWL_OK;
+}
+
 template <class T>
 static cudaError_t dget(std::vector<T> &v, const T *d, size_t n)
 {
@@ -795,6 +849,7 @@ static void join_pieces(const HostInst &h, const std::vector<double> &pieces, st
     const double dE = I.step;
     out.assign(B, NAN);
     auto piece = [&](int i, int b) { return pieces[(size_t)i * w + (b - h.lo[i])]; };
+    const std::vector<int> &ww = h.ww;
     auto beta = [&](int i, int b) {
         return (piece(i, b - 2 * s) - 8.0 * piece(i, b - s) + 8.0 * piece(i, b + s) - piece(i, b + 2 * s)) /
                (12.0 * s * dE);
@@ -803,7 +858,7 @@ static void join_pieces(const HostInst &h, const std::vector<double> &pieces, st
     int start = h.lo[0];
     for (int i = 0; i + 1 < H; ++i) {
         const int ov_lo = std::max(h.lo[i], h.lo[i + 1]);
-        const int ov_hi = std::min(h.lo[i] + w - 1, h.lo[i + 1] + w - 1);
+        const int ov_hi = std::min(h.lo[i] + ww[i] - 1, h.lo[i + 1] + ww[i + 1] - 1);
         int best = -1;
         double best_d = 0.0;
         for (int b = std::max(ov_lo, start + 1); b <= ov_hi; ++b) {
@@ -825,7 +880,7 @@ static void join_pieces(const HostInst &h, const std::vector<double> &pieces, st
         shift = piece(i, best) + shift - piece(i + 1, best);
         start = best;
     }
-    for (int b = start; b < h.lo[H - 1] + w; ++b) out[b] = piece(H - 1, b) + shift;
+    for (int b = start; b < h.lo[H - 1] + ww[H - 1]; ++b) out[b] = piece(H - 1, b) + shift;
     int first = -1;
     for (int b = 0; b < B; ++b) {
         if (!h.reach[b]) out[b] = NAN;
@@ -854,7 +909,7 @@ extern "C" rewl_status rewl_get_dos(rewl_ctx *ctx, int inst, double *ln_g, long 
         for (int b = 0; b < I.w; ++b) {
             double acc = 0.0;
             for (int j = 0; j < I.m; ++j) acc += std::ldexp((double)u[((size_t)i * I.m + j) * I.w + b], -32);
-            pieces[(size_t)i * I.w + b] = acc / I.m;
+            pieces[(size_t)i * I.w + b] = b < h.ww[i] ? acc / I.m : NAN;
         }
     if (per_window) {
         std::copy(pieces.begin(), pieces.end(), ln_g);
@@ -889,7 +944,7 @@ extern "C" rewl_status rewl_set_initial_lng(rewl_ctx *ctx, int inst, const doubl
     const InstDev &I = h.dev;
     std::vector<long long> u((size_t)I.h * I.m * I.w);
     for (int i = 0; i < I.h; ++i)
-        for (int b = 0; b < I.w; ++b) {
+        for (int b = 0; b < h.ww[i]; ++b) {
             double v = ln_g0[h.lo[i] + b];
             if (!std::isfinite(v)) v = 0.0;
             const double units = std::nearbyint(std::ldexp(v, 32));
@@ -976,7 +1031,7 @@ extern "C" const char *rewl_last_error(const rewl_ctx *ctx)
 // ---------------------------------------------------------------------------
 // checkpoint
 // ---------------------------------------------------------------------------
-static const char kMagic[8] = {'R', 'E', 'W', 'L', 'C', 'K', 'P', '2'};
+static const char kMagic[8] = {'R', 'E', 'W', 'L', 'C', 'K', 'P', '3'};
 
 template <class T>
 static bool wr(FILE *f, const std::vector<T> &v)
@@ -1026,6 +1081,13 @@ extern "C" rewl_status rewl_save(rewl_ctx *ctx, const char *path)
     ok = ok && wr(f, desc);
     std::vector<long> opts = {ctx->check_every};
     ok = ok && wr(f, opts);
+    std::vector<int32_t> wlo, whi;                   // every window, bin by bin
+    for (auto &h : ctx->inst)
+        for (int i = 0; i < h.dev.h; ++i) {
+            wlo.push_back(h.lo[i]);
+            whi.push_back(h.lo[i] + h.ww[i] - 1);
+        }
+    ok = ok && wr(f, wlo) && wr(f, whi);
 #define SAVE_ONE(T, field, n)                                     \
     if (ok) {                                                     \
         std::vector<T> v;                                         \
@@ -1048,12 +1110,19 @@ extern "C" rewl_status rewl_load(rewl_ctx **out, const char *path, void *cuda_st
     char mg[8];
     std::vector<rewl_instance> desc;
     std::vector<long> opts;
-    bool ok = fread(mg, 8, 1, f) == 1 && memcmp(mg, kMagic, 8) == 0 && rd(f, desc) && rd(f, opts) && !desc.empty();
+    std::vector<int32_t> wlo, whi;
+    bool ok = fread(mg, 8, 1, f) == 1 && memcmp(mg, kMagic, 8) == 0 && rd(f, desc) && rd(f, opts) && !desc.empty() &&
+              rd(f, wlo) && rd(f, whi) && wlo.size() == whi.size();
+    if (ok) {
+        size_t total = 0;
+        for (auto &d : desc) total += d.n_windows > 0 ? (size_t)d.n_windows : 0;
+        ok = total == wlo.size();
+    }
     if (!ok) {
         fclose(f);
         return fail(nullptr, REWL_EINVAL, std::string(path) + " is not a REWL checkpoint");
     }
-    rewl_status s = rewl_create_batch(out, desc.data(), (int)desc.size(), cuda_stream);
+    rewl_status s = create_batch(out, desc.data(), (int)desc.size(), wlo.data(), whi.data(), cuda_stream);
     if (s) {
         fclose(f);
         return s;

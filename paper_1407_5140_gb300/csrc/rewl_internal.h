@@ -60,6 +60,7 @@ struct DevState {
     const InstDev *inst;
     // per window (global index)
     const int32_t *lo;
+    const int32_t *ww;        // bins of the window (InstDev::w is the widest)
     const int32_t *n_reach;
     int32_t *stage;
     uint8_t *conv;

@@ -52,7 +52,7 @@ __global__ void init_kernel(DevState st, int n_slots, const int32_t *slot_inst)
     const int local = slot - I.slot0;
     const int win = local / I.m, j = local % I.m;
     const int gwin = I.win0 + win;
-    const int lo = st.lo[gwin], hi = lo + I.w - 1;
+    const int lo = st.lo[gwin], hi = lo + st.ww[gwin] - 1;
     const int L = I.L, N = I.N;
     uint32_t *lat = st.lat + I.lat_off + (long long)local * I.lat_words;
     st.cfg[slot] = local;
@@ -128,7 +128,7 @@ int sweep_smem_bytes(int n_walkers, int n_win, int w, int lat_words)
     b += (long long)n_walkers * 8;                      // Philox draw counters
     b += (long long)n_walkers * (lat_words | 1) * 4;    // lattices, odd word stride
     b += ((long long)n_win * w + 15) / 16 * 16;         // reach
-    b += (long long)n_win * 16;                         // window state
+    b += (long long)n_win * 20;                         // window state
     b += ((long long)n_walkers + 15) / 16 * 16;         // latch
     b += 2LL * n_walkers * 4;                           // near masks, 2 slots
     return (int)b;
@@ -354,7 +354,8 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
     int *wconv_s = wst_s + n_win;
     int *wmerge_s = wst_s + 2 * n_win;
     int *wgwin_s = wst_s + 3 * n_win;
-    uint8_t *latch_s = reinterpret_cast<uint8_t *>(wst_s + 4 * n_win);
+    int *wwid_s = wst_s + 4 * n_win;        // bins of each window
+    uint8_t *latch_s = reinterpret_cast<uint8_t *>(wst_s + 5 * n_win);
     // per slot and walker: bit a set when trial a of the round is near trial a - 1
     uint32_t *nearm_s = reinterpret_cast<uint32_t *>(latch_s + (nw + 15) / 16 * 16);
 
@@ -374,11 +375,13 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
     }
     for (int i = tid; i < n_win * w; i += nthreads) {
         const int wl = i / w, bb = i - wl * w;
-        reach_s[i] = st.reach[I.reach_off + st.lo[I.win0 + it.win_begin + wl] + bb];
+        const int gw = I.win0 + it.win_begin + wl;
+        reach_s[i] = bb < st.ww[gw] ? st.reach[I.reach_off + st.lo[gw] + bb] : (uint8_t)0;
     }
     for (int i = tid; i < n_win; i += nthreads) {
         const int gwin = I.win0 + it.win_begin + i;
         wgwin_s[i] = gwin;
+        wwid_s[i] = st.ww[gwin];
         wstage_s[i] = st.stage[gwin];
         wconv_s[i] = st.conv[gwin];
         wmerge_s[i] = 0;
@@ -393,6 +396,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
     // consumer state (lane tv)
     const int wl_c = tv / m;
     const int lo = st.lo[I.win0 + it.win_begin + wl_c];
+    const int w_c = st.ww[I.win0 + it.win_begin + wl_c];   // the lane's window width
     int b = st.bin[slot_base + tv];
     long long *lng = lng_s + (size_t)tv * wg + kGuard - lo;   // indexed by global bin
     uint32_t *H = Hblk + (size_t)tv * w - lo;                  // global, indexed by global bin
@@ -515,7 +519,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                         }
                         // accept iff ln g(E') < ln g(E) + lam, i.e. with min(1, g(E)/g(E'))
                         const int bn = b + db;
-                        const bool inw = (unsigned)(bn - lo) < (unsigned)w;
+                        const bool inw = (unsigned)(bn - lo) < (unsigned)w_c;
                         const long long thr = cur + t.lam;
                         // ln g of the proposed bin (shared memory holds cur at b,
                         // and guard cells beyond the window's edges)
@@ -578,7 +582,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                 const int shift = 32 - wstage_s[wlk];   // ln f = 2^(32 - stage) units
                 unsigned long long mn = ~0ull, sum = 0ull;
                 long long amax = 0;
-                for (int bb = lane; bb < w; bb += 32) {
+                for (int bb = lane; bb < wwid_s[wlk]; bb += 32) {
                     const long long v = lk[bb];
                     const long long av = v < 0 ? -v : v;
                     amax = av > amax ? av : amax;
@@ -619,7 +623,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
             // to even); the next stage starts from it (lng0 <- ln g, H <- 0)
             for (int i = tid; i < n_win * w; i += nthreads) {
                 const int ww = i / w, bb = i - ww * w;
-                if (!wmerge_s[ww]) continue;
+                if (!wmerge_s[ww] || bb >= wwid_s[ww]) continue;
                 long long sacc = 0;
                 for (int jj = 0; jj < m; ++jj) sacc += lng_s[(size_t)(ww * m + jj) * wg + kGuard + bb];
                 const long long mean = div_round_even(sacc, m);
@@ -721,7 +725,7 @@ __global__ void exchange_kernel(DevState st, const ExTask *t0, int n0, const ExT
     atomicAdd(&st.ex_prop[gw_a], 1ull);
     const int lo_a = st.lo[gw_a], lo_b = st.lo[gw_b];
     const int bx = st.bin[a], by = st.bin[bslot];
-    if (bx < lo_b || bx > lo_b + w - 1 || by < lo_a || by > lo_a + w - 1) return;
+    if (bx < lo_b || bx > lo_b + st.ww[gw_b] - 1 || by < lo_a || by > lo_a + st.ww[gw_a] - 1) return;
     const long long *ga = st.lng + I.lng_off + (long long)(i * m + j) * w;
     const long long *gb = st.lng + I.lng_off + (long long)((i + 1) * m + (j + shift) % m) * w;
     // -ln of the Eq. (1) ratio, in 2^-32 units

@@ -270,10 +270,10 @@ __global__ void install_kernel(DevState st, int inst, const float *s_pred, int k
 {
     const InstDev I = st.inst[inst];
     const int i = blockIdx.x;                       // window
-    const int w = I.w, gwin = I.win0 + i, lo = st.lo[gwin];
+    const int w = I.w, gwin = I.win0 + i, lo = st.lo[gwin], wi = st.ww[gwin];   // row length, window width
     __shared__ float red[256];
     float mn = 3.4e38f;
-    for (int b = threadIdx.x; b < w; b += blockDim.x)
+    for (int b = threadIdx.x; b < wi; b += blockDim.x)
         if (st.reach[I.reach_off + lo + b]) mn = fminf(mn, (float)I.N * s_pred[(size_t)i * w + b]);
     red[threadIdx.x] = mn;
     __syncthreads();
@@ -283,7 +283,8 @@ __global__ void install_kernel(DevState st, int inst, const float *s_pred, int k
     }
     mn = red[0];
     for (int b = threadIdx.x; b < w; b += blockDim.x) {
-        const double v = st.reach[I.reach_off + lo + b] ? (double)((float)I.N * s_pred[(size_t)i * w + b] - mn) : 0.0;
+        const double v = (b < wi && st.reach[I.reach_off + lo + b]) ? (double)((float)I.N * s_pred[(size_t)i * w + b] - mn)
+                                                                    : 0.0;
         const long long units = llrint(v * 4294967296.0);
         for (int j = 0; j < I.m; ++j) {
             const long long off = I.lng_off + (long long)(i * I.m + j) * w + b;

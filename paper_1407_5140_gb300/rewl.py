@@ -47,6 +47,8 @@ def lib():
         vp, i32, i64, u32, u64, f64 = C.c_void_p, C.c_int, C.c_long, C.c_uint32, C.c_uint64, C.c_double
         L.rewl_create.argtypes = [C.POINTER(vp), i32, i32, i32, i64, i64, i32, f64, i32, f64, f64, u64, vp]
         L.rewl_create_batch.argtypes = [C.POINTER(vp), C.POINTER(rewl_instance), i32, vp]
+        L.rewl_create_batch_windows.argtypes = [C.POINTER(vp), C.POINTER(rewl_instance), i32, vp, vp, vp]
+        L.rewl_window_widths.argtypes = [vp, i32, vp]
         L.rewl_run.argtypes = [vp, i64]
         L.rewl_exchange.argtypes = [vp]
         L.rewl_run_cycles.argtypes = [vp, i64, i64]
@@ -124,7 +126,9 @@ def instance(model, L, q=2, e_min=None, e_max=None, n_windows=1, overlap=0.75, w
 class Rewl:
     """A REWL context: one or more independent instances sampled together."""
 
-    def __init__(self, instances, stream=None, _handle=None):
+    def __init__(self, instances, stream=None, _handle=None, windows=None):
+        """windows: None (equal-width windows from each instance's overlap) or one
+        (lo, hi) pair of bin-index arrays per instance (rewl_create_batch_windows)."""
         self._h = C.c_void_p()
         if _handle is not None:
             self._h = _handle
@@ -132,7 +136,13 @@ class Rewl:
             if isinstance(instances, rewl_instance):
                 instances = [instances]
             arr = (rewl_instance * len(instances))(*instances)
-            code = lib().rewl_create_batch(C.byref(self._h), arr, len(instances), _stream_ptr(stream))
+            if windows is None:
+                code = lib().rewl_create_batch(C.byref(self._h), arr, len(instances), _stream_ptr(stream))
+            else:
+                lo = np.ascontiguousarray(np.concatenate([np.asarray(w[0]) for w in windows]), dtype=np.int32)
+                hi = np.ascontiguousarray(np.concatenate([np.asarray(w[1]) for w in windows]), dtype=np.int32)
+                code = lib().rewl_create_batch_windows(C.byref(self._h), arr, len(instances), _p(lo), _p(hi),
+                                                       _stream_ptr(stream))
             if code != 0:
                 msg = lib().rewl_last_error(self._h if self._h else None).decode()
                 if self._h:
@@ -228,7 +238,9 @@ class Rewl:
             lo = np.zeros(h.value, np.int32)
             reach = np.zeros(B.value, np.uint8)
             _check(lib().rewl_geometry(self._h, inst, None, None, None, None, _p(lo), _p(reach)), self._h)
-            self._geom[inst] = dict(h=h.value, m=m.value, B=B.value, w=w.value, lo=lo, reach=reach)
+            ww = np.zeros(h.value, np.int32)
+            _check(lib().rewl_window_widths(self._h, inst, _p(ww)), self._h)
+            self._geom[inst] = dict(h=h.value, m=m.value, B=B.value, w=w.value, lo=lo, reach=reach, ww=ww)
         return self._geom[inst]
 
     def status(self, inst=0):

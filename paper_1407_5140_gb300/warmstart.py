@@ -16,12 +16,14 @@ from . import rewl as R
 
 
 def curve_samples(model, L, q, e_min, step, ln_g, lo, w):
-    """(x, t) samples of one joined ln g curve: one per (window, realisable bin)."""
+    """(x, t) samples of one joined ln g curve: one per (window, realisable bin);
+    w: bins per window (one number, or one per window)."""
     N = L * L
     h = len(lo)
+    ws = np.broadcast_to(np.asarray(w), (h,))
     xs, ts = [], []
     for i, l0 in enumerate(lo):
-        for b in range(l0, l0 + w):
+        for b in range(l0, l0 + int(ws[i])):
             v = ln_g[b]
             if not np.isfinite(v):
                 continue
@@ -39,7 +41,7 @@ def training_set(ctx, instances):
         ln_g, _ = ctx.get_dos(k)
         step = 4 if d["model"] == R.ISING else 1
         q = 2 if d["model"] == R.ISING else d["q"]
-        x, t = curve_samples(d["model"], d["L"], q, d["e_min"], step, ln_g, g["lo"], g["w"])
+        x, t = curve_samples(d["model"], d["L"], q, d["e_min"], step, ln_g, g["lo"], g["ww"])
         X.append(x)
         T.append(t)
     return np.concatenate(X), np.concatenate(T)

@@ -5,15 +5,16 @@ import numpy as np
 import oracle as O
 
 
-def make_oracle(d, threads=0):
+def make_oracle(d, threads=0, windows=None):
     return O.Oracle(d["model"], d["L"], d["q"], d["e_min"], d["e_max"], d["n_windows"], d["overlap"],
                     d["walkers_per_window"], d["flatness"], d["ln_f_final"], seed=d["seed"],
-                    instance=d["instance_id"], threads=threads, flat_rule=d.get("flat_rule", 0))
+                    instance=d["instance_id"], threads=threads, flat_rule=d.get("flat_rule", 0),
+                    windows=windows)
 
 
-def make_gpu(ds, **opts):
+def make_gpu(ds, windows=None, **opts):
     from paper_1407_5140_gb300 import rewl as R
-    ctx = R.Rewl([R.instance(**d) for d in ds])
+    ctx = R.Rewl([R.instance(**d) for d in ds], windows=windows)
     for k, v in opts.items():
         ctx.set_option(getattr(R, "OPT_" + k.upper()), v)
     return ctx

@@ -233,6 +233,55 @@ def test_learned_warm_start_install_then_bit_exact():
     net.close()
 
 
+UNEVEN = [
+    ("ising_L8_uneven", _ising(8, 4, 2, seed=51), ([0, 14, 30, 44], [24, 38, 52, 64]), 40, 3),
+    ("ising_L16_uneven5", _ising(16, 5, 3, seed=52), ([0, 40, 90, 150, 200], [70, 120, 180, 230, 256]), 25, 3),
+    ("potts_q3_L6_uneven", _potts(6, 3, 3, 2, seed=53), ([0, 20, 45], [35, 60, 72]), 40, 3),
+]
+
+
+@pytest.mark.parametrize("name,d,win,sweeps,cycles", UNEVEN, ids=[c[0] for c in UNEVEN])
+def test_uneven_windows_match_oracle(name, d, win, sweeps, cycles):
+    """Windows of different widths (rewl_create_batch_windows, Sec. V): state,
+    exchanges and the joined DOS bit-exact / equal to the oracle's."""
+    gpu = make_gpu([d], windows=[win])
+    orc = make_oracle(d, windows=win)
+    orc.init()
+    g = gpu.geometry(0)
+    assert list(g["lo"]) == list(orc.lo) and list(g["ww"]) == list(orc.ww) and g["w"] == orc.w
+    assert_same_state(gpu, 0, orc, f"{name} after init")
+    for c in range(cycles):
+        step_both(gpu, [orc], sweeps)
+        assert_same_state(gpu, 0, orc, f"{name} cycle {c}")
+    lg, _ = gpu.get_dos(0)
+    olg, _ = cc.concatenate(orc.pieces(), orc.lo, orc.ww, orc.reach, 4.0 if d["model"] == 0 else 1.0,
+                            math.log(2 if d["model"] == 0 else d["q"]))
+    assert np.allclose(lg, olg, equal_nan=True, atol=1e-9)
+
+
+def test_uneven_windows_invalid_and_checkpoint(tmp_path):
+    from paper_1407_5140_gb300 import rewl as R
+    d = _ising(8, 4, 2, seed=54)
+    for lo, hi in [([1, 14, 30, 44], [24, 38, 52, 64]), ([0, 25, 30, 44], [24, 38, 52, 64]),
+                   ([0, 14, 30, 44], [24, 38, 52, 63]), ([0, 14, 30, 62], [24, 38, 52, 64])]:
+        with pytest.raises(R.RewlError) as ei:
+            make_gpu([d], windows=[(lo, hi)])
+        assert ei.value.code == -1
+    win = ([0, 14, 30, 44], [24, 38, 52, 64])
+    a = make_gpu([d], windows=[win])
+    a.run(50)
+    a.exchange()
+    path = str(tmp_path / "uneven.ckpt")
+    a.save(path)
+    b = R.Rewl.load(path)
+    assert list(b.geometry(0)["ww"]) == [25, 25, 23, 21]
+    a.run(30)
+    b.run(30)
+    sa, sb = a.state(0, 64), b.state(0, 64)
+    for key in ("spins", "lng", "H", "bin", "stage"):
+        assert np.array_equal(np.asarray(sa[key]), np.asarray(sb[key])), key
+
+
 def test_empty_batch_is_rejected():
     from paper_1407_5140_gb300 import rewl as R
     with pytest.raises(R.RewlError) as ei:
