@@ -484,6 +484,61 @@ def exchange_study_workload(intervals=(100, 1000, 10000, 0), cap_s=600.0):
                       "workload": "q=10 Potts 48x48, 15 windows at 75%, m=1, 8 seeds", "results": res}))
 
 
+def balanced_windows_workload(seeds=8, L=48, q=10, h=15, overlap=0.75, exchange_interval=1000, cap_s=600.0):
+    """Run-time-balanced windows (Sec. V): a pilot run with equal windows
+    measures the sweeps each window's slowest walker needs for the first WL
+    iteration; windows resized by (t_mean / t)^(1/2) are then compared with
+    equal ones on fresh seeds -- sweeps of the slowest window for the first
+    iteration and for the first eight (q = 10 Potts 48 x 48, 15 windows, one
+    walker each, exchanges every 10^3 sweeps)."""
+    import numpy as np
+    import torch
+    from paper_1407_5140_gb300 import rewl as R
+    from paper_1407_5140_gb300 import thermo as TH
+    from paper_1407_5140_gb300 import windows as WN
+    from paper_1407_5140_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    B = 2 * L * L + 1
+    elo, ehi = WN.equal_windows(B, h, overlap)
+
+    def run(seed0, win, finals):
+        ds = [W._inst(W.POTTS, L, q, h, 1, seed0 + 10 * s + j, ln_f_final=f)
+              for s in range(seeds) for j, f in enumerate(finals)]
+        ctx = R.Rewl([R.instance(**d) for d in ds], stream=stream, windows=[win] * len(ds))
+        t0 = time.perf_counter()
+        done = ctx.run_to_convergence(exchange_interval, 0)
+        while not done and time.perf_counter() - t0 < cap_s:
+            done = ctx.run_to_convergence(exchange_interval, 20 * exchange_interval, poll_cycles=20)
+        secs = time.perf_counter() - t0
+        per = {f: [ctx.counters(k)["conv_sweep"] for k, d in enumerate(ds) if d["ln_f_final"] == f] for f in finals}
+        ctx.close()
+        return per, secs, bool(done)
+
+    pilot, t_pilot, ok_pilot = run(20000, (elo, ehi), [1.0])
+    t_win = np.mean(np.array(pilot[1.0], float), axis=0)          # per window, mean over seeds
+    blo, bhi = WN.balanced_windows(elo, ehi, t_win, B, overlap, 9)
+    out = {"metric": "sweeps to finish WL iterations, equal vs run-time-balanced windows", "n_gpus": 1,
+           "data": "synthetic", "workload": f"q={q} Potts {L}x{L}, {h} windows at {int(overlap * 100)}%, m=1, "
+                                             f"{seeds} seeds", "pilot_seconds": t_pilot, "pilot_converged": ok_pilot,
+           "pilot_window_sweeps": t_win.tolist(), "equal": {"lo": elo.tolist(), "hi": ehi.tolist()},
+           "balanced": {"lo": blo.tolist(), "hi": bhi.tolist()}}
+    for name, win in (("equal", (elo, ehi)), ("balanced", (blo, bhi))):
+        per, secs, ok = run(30000, win, [1.0, 2.0 ** -7])
+        first = np.array([c.max() for c in per[1.0]], float)
+        eight = np.array([c.max() for c in per[2.0 ** -7]], float)
+        m1, e1 = TH.bootstrap(first, seed=1)
+        m8, e8 = TH.bootstrap(eight, seed=8)
+        out[name].update({"seconds": secs, "converged": ok, "first_iteration_mean": m1, "first_iteration_err": e1,
+                          "eight_iterations_mean": m8, "eight_iterations_err": e8,
+                          "first_iteration_per_window": np.mean([c for c in per[1.0]], axis=0).tolist()})
+    out["speedup_first"] = out["equal"]["first_iteration_mean"] / out["balanced"]["first_iteration_mean"]
+    out["speedup_eight"] = out["equal"]["eight_iterations_mean"] / out["balanced"]["eight_iterations_mean"]
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -493,10 +548,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--profile-case", action="store_true",
                     help="only the workload's launch shape with 20 sweeps per launch (for ncu captures)")
-    ap.add_argument("--workload", default="throughput", choices=["throughput", "warm-start", "potts-tc", "exchange"],
+    ap.add_argument("--workload", default="throughput", choices=["throughput", "warm-start", "potts-tc", "exchange", "balanced-windows"],
                     help="warm-start: time to converge, learned vs plain (Ising L=128, Potts q=10 L=64); "
                          "potts-tc: q=10 Potts transition from C_v maxima, L=16..64; "
-                         "exchange: sweeps to finish WL iterations vs exchange frequency")
+                         "exchange: sweeps to finish WL iterations vs exchange frequency; "
+                         "balanced-windows: equal vs run-time-balanced windows")
     args = ap.parse_args()
     if args.profile_case:
         profile_case()
@@ -509,6 +565,9 @@ def main():
         return
     if args.workload == "exchange":
         exchange_study_workload()
+        return
+    if args.workload == "balanced-windows":
+        balanced_windows_workload()
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
