@@ -539,6 +539,60 @@ def balanced_windows_workload(seeds=8, L=48, q=10, h=15, overlap=0.75, exchange_
     print(json.dumps(out))
 
 
+def balanced_converge_workload(seeds=4, L=64, q=10, h=64, m=4, overlap=0.75, exchange_interval=1000,
+                               cap_s=900.0):
+    """Time to ln f = 2^-20 on equal and on run-time-balanced windows (Sec. V):
+    q = 10 Potts L = 64, 64 windows x 4 walkers; a first-iteration pilot on
+    equal windows sizes the balanced set, then fresh seeds run to convergence
+    on each.  Reports sweeps of the slowest window, wall time, and how far the
+    two DOS agree (and ln sum g - N ln q)."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1407_5140_gb300 import rewl as R
+    from paper_1407_5140_gb300 import windows as WN
+    from paper_1407_5140_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    B = 2 * L * L + 1
+    elo, ehi = WN.equal_windows(B, h, overlap)
+
+    def run(seed0, win, final):
+        ds = [W._inst(W.POTTS, L, q, h, m, seed0 + s, ln_f_final=final) for s in range(seeds)]
+        ctx = R.Rewl([R.instance(**d) for d in ds], stream=stream, windows=[win] * seeds)
+        ctx.run(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ok = _converge(ctx, exchange_interval, 5, cap_s, f"L={L} {'pilot' if final == 1.0 else 'run'}")
+        secs = time.perf_counter() - t0
+        conv = [ctx.counters(k)["conv_sweep"] for k in range(seeds)]
+        dos = [ctx.get_dos(k)[0] for k in range(seeds)]
+        ctx.close()
+        return conv, dos, secs, ok
+
+    pconv, _, psecs, pok = run(40000, (elo, ehi), 1.0)
+    t_win = np.mean(np.array(pconv, float), axis=0)
+    blo, bhi = WN.balanced_windows(elo, ehi, t_win, B, overlap, 9)
+    out = {"metric": "time to ln f=2^-20, equal vs run-time-balanced windows", "unit": "s", "n_gpus": 1,
+           "data": "synthetic", "workload": f"q={q} Potts L={L}, {h} windows x {m} walkers, {seeds} seeds",
+           "pilot_seconds": psecs, "pilot_converged": pok,
+           "balanced_widths": (bhi - blo + 1).tolist()}
+    res = {}
+    for name, win in (("equal", (elo, ehi)), ("balanced", (blo, bhi))):
+        conv, dos, secs, ok = run(41000 if name == "equal" else 42000, win, 2.0 ** -20)
+        sw = [int(c.max()) for c in conv]
+        res[name] = dos
+        out[name] = {"seconds": secs, "converged": ok, "sweeps_slowest_window": sw, "mean_sweeps": float(np.mean(sw)),
+                     "log_sum_minus_N_ln_q": [_log_sum(lg) - L * L * math.log(q) for lg in dos]}
+    out["eps_balanced_vs_equal"] = [_mean_rel_err(a, b) for a, b in zip(res["balanced"], res["equal"])]
+    out["eps_equal_seed_to_seed"] = [_mean_rel_err(res["equal"][k], res["equal"][0]) for k in range(1, seeds)]
+    out["sweep_ratio_balanced_over_equal"] = out["balanced"]["mean_sweeps"] / out["equal"]["mean_sweeps"]
+    out["time_ratio_balanced_over_equal"] = out["balanced"]["seconds"] / out["equal"]["seconds"]
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -548,11 +602,13 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--profile-case", action="store_true",
                     help="only the workload's launch shape with 20 sweeps per launch (for ncu captures)")
-    ap.add_argument("--workload", default="throughput", choices=["throughput", "warm-start", "potts-tc", "exchange", "balanced-windows"],
+    ap.add_argument("--workload", default="throughput", choices=["throughput", "warm-start", "potts-tc", "exchange", "balanced-windows",
+                             "balanced-converge"],
                     help="warm-start: time to converge, learned vs plain (Ising L=128, Potts q=10 L=64); "
                          "potts-tc: q=10 Potts transition from C_v maxima, L=16..64; "
                          "exchange: sweeps to finish WL iterations vs exchange frequency; "
-                         "balanced-windows: equal vs run-time-balanced windows")
+                         "balanced-windows: equal vs run-time-balanced windows; "
+                         "balanced-converge: time to converge on equal vs balanced windows (Potts q=10 L=64)")
     args = ap.parse_args()
     if args.profile_case:
         profile_case()
@@ -568,6 +624,9 @@ def main():
         return
     if args.workload == "balanced-windows":
         balanced_windows_workload()
+        return
+    if args.workload == "balanced-converge":
+        balanced_converge_workload()
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
