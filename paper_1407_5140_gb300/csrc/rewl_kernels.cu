@@ -2,12 +2,16 @@
 //
 //  init_kernel      one thread per walker: start configuration, random walk into
 //                   the walker's energy window (stream 1 of its Philox key).
-//  sweep_kernel     one thread block per group of whole windows; each walker is
-//                   served by G lanes of a warp.  The block copies its walkers'
-//                   lattices, ln g and H into shared memory, runs n sweeps of
-//                   Wang-Landau trials (Sec. II A), and after every check_every
-//                   sweeps tests flatness and merges windows whose m walkers are
-//                   all flat (warp shuffles for the per-walker reductions).
+//  sweep_kernel     one thread block per group of whole windows (at most 32
+//                   walkers): producer warps prepare the state-independent part
+//                   of every trial (Philox draws, sites, thresholds) a round
+//                   ahead, and one consumer warp resolves each walker's trials
+//                   in draw order, one lane per walker.  The block copies its
+//                   walkers' lattices and ln g into shared memory, runs n sweeps
+//                   of Wang-Landau trials (Sec. II A), and after every
+//                   check_every sweeps tests flatness (H read off ln g and its
+//                   value at the stage start; warp shuffles for the per-walker
+//                   reductions) and merges windows whose m walkers are all flat.
 //  exchange_kernel  one thread per proposed swap of a window pair (Eq. (1),
 //                   Fig. 2); swaps the configuration indices of the two slots.
 //  bump_kernel      advances the device-side sweep / exchange counters, so a
