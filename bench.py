@@ -540,7 +540,7 @@ def balanced_windows_workload(seeds=8, L=48, q=10, h=15, overlap=0.75, exchange_
 
 
 def balanced_converge_workload(seeds=4, L=64, q=10, h=64, m=4, overlap=0.75, exchange_interval=1000,
-                               cap_s=900.0):
+                               cap_s=900.0, model=1, compare_equal=True):
     """Time to ln f = 2^-20 on equal and on run-time-balanced windows (Sec. V):
     q = 10 Potts L = 64, 64 windows x 4 walkers; a first-iteration pilot on
     equal windows sizes the balanced set, then fresh seeds run to convergence
@@ -556,11 +556,12 @@ def balanced_converge_workload(seeds=4, L=64, q=10, h=64, m=4, overlap=0.75, exc
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    B = 2 * L * L + 1
+    B = 2 * L * L + 1 if model == W.POTTS else L * L + 1
+    min_w = 9 if model == W.POTTS else 5
     elo, ehi = WN.equal_windows(B, h, overlap)
 
     def run(seed0, win, final):
-        ds = [W._inst(W.POTTS, L, q, h, m, seed0 + s, ln_f_final=final) for s in range(seeds)]
+        ds = [W._inst(model, L, q, h, m, seed0 + s, ln_f_final=final) for s in range(seeds)]
         ctx = R.Rewl([R.instance(**d) for d in ds], stream=stream, windows=[win] * seeds)
         ctx.run(1)
         torch.cuda.synchronize()
@@ -574,22 +575,28 @@ def balanced_converge_workload(seeds=4, L=64, q=10, h=64, m=4, overlap=0.75, exc
 
     pconv, _, psecs, pok = run(40000, (elo, ehi), 1.0)
     t_win = np.mean(np.array(pconv, float), axis=0)
-    blo, bhi = WN.balanced_windows(elo, ehi, t_win, B, overlap, 9)
+    blo, bhi = WN.balanced_windows(elo, ehi, t_win, B, overlap, min_w)
+    name_m = f"q={q} Potts" if model == W.POTTS else "Ising"
     out = {"metric": "time to ln f=2^-20, equal vs run-time-balanced windows", "unit": "s", "n_gpus": 1,
-           "data": "synthetic", "workload": f"q={q} Potts L={L}, {h} windows x {m} walkers, {seeds} seeds",
+           "data": "synthetic", "workload": f"{name_m} L={L}, {h} windows x {m} walkers, {seeds} seeds",
            "pilot_seconds": psecs, "pilot_converged": pok,
            "balanced_widths": (bhi - blo + 1).tolist()}
     res = {}
-    for name, win in (("equal", (elo, ehi)), ("balanced", (blo, bhi))):
+    sets = (("equal", (elo, ehi)), ("balanced", (blo, bhi))) if compare_equal else (("balanced", (blo, bhi)),)
+    for name, win in sets:
         conv, dos, secs, ok = run(41000 if name == "equal" else 42000, win, 2.0 ** -20)
         sw = [int(c.max()) for c in conv]
         res[name] = dos
         out[name] = {"seconds": secs, "converged": ok, "sweeps_slowest_window": sw, "mean_sweeps": float(np.mean(sw)),
-                     "log_sum_minus_N_ln_q": [_log_sum(lg) - L * L * math.log(q) for lg in dos]}
-    out["eps_balanced_vs_equal"] = [_mean_rel_err(a, b) for a, b in zip(res["balanced"], res["equal"])]
-    out["eps_equal_seed_to_seed"] = [_mean_rel_err(res["equal"][k], res["equal"][0]) for k in range(1, seeds)]
-    out["sweep_ratio_balanced_over_equal"] = out["balanced"]["mean_sweeps"] / out["equal"]["mean_sweeps"]
-    out["time_ratio_balanced_over_equal"] = out["balanced"]["seconds"] / out["equal"]["seconds"]
+                     "log_sum_minus_N_ln_q": [_log_sum(lg) - L * L * math.log(q if model == W.POTTS else 2)
+                                              for lg in dos]}
+        if model == W.ISING:
+            out[name]["eps_vs_exact"] = [_mean_rel_err(lg, _golden_ising(L)) for lg in dos]
+    if compare_equal:
+        out["eps_balanced_vs_equal"] = [_mean_rel_err(a, b) for a, b in zip(res["balanced"], res["equal"])]
+        out["eps_equal_seed_to_seed"] = [_mean_rel_err(res["equal"][k], res["equal"][0]) for k in range(1, seeds)]
+        out["sweep_ratio_balanced_over_equal"] = out["balanced"]["mean_sweeps"] / out["equal"]["mean_sweeps"]
+        out["time_ratio_balanced_over_equal"] = out["balanced"]["seconds"] / out["equal"]["seconds"]
     print(json.dumps(out))
 
 
@@ -603,7 +610,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="only the workload's launch shape with 20 sweeps per launch (for ncu captures)")
     ap.add_argument("--workload", default="throughput", choices=["throughput", "warm-start", "potts-tc", "exchange", "balanced-windows",
-                             "balanced-converge"],
+                             "balanced-converge", "balanced-converge-ising"],
                     help="warm-start: time to converge, learned vs plain (Ising L=128, Potts q=10 L=64); "
                          "potts-tc: q=10 Potts transition from C_v maxima, L=16..64; "
                          "exchange: sweeps to finish WL iterations vs exchange frequency; "
@@ -627,6 +634,9 @@ def main():
         return
     if args.workload == "balanced-converge":
         balanced_converge_workload()
+        return
+    if args.workload == "balanced-converge-ising":      # Ising L=128, balanced windows only
+        balanced_converge_workload(L=128, q=2, model=0, compare_equal=False)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
