@@ -39,24 +39,36 @@ def _layout(widths, overlap, B):
     return np.array(lo, np.int64), np.array(hi, np.int64), hi[-1]
 
 
-def balanced_windows(lo, hi, t, B, overlap, min_width):
+def balanced_windows(lo, hi, t, B, overlap, min_width, max_width=None):
     """Windows sized so that each should finish a WL iteration in about the
     same number of sweeps: widths w_i (t_mean / t_i)^(1/2), same overlap rule,
     scaled to cover bins 0..B-1 exactly; every window at least min_width
-    wide.  t: sweeps of each window's slowest walker in a pilot run."""
+    wide and, if max_width is given, at most that wide (each walker's ln g row
+    in shared memory is as long as the widest window, so very wide windows
+    cost occupancy).  t: sweeps of each window's slowest walker in a pilot
+    run."""
     lo = np.asarray(lo, np.float64)
     hi = np.asarray(hi, np.float64)
     t = np.asarray(t, np.float64)
     rel = (hi - lo + 1.0) * np.sqrt(t.mean() / np.maximum(t, 1.0))
+    cap = np.inf if max_width is None else float(max_width)
+
+    def widths(scale):
+        return np.minimum(np.maximum(rel * scale, min_width), cap)
+
     a, b = 1e-6, 4.0 * B / rel.sum() + 1.0        # scale factors bracketing the span
+    if max_width is not None and _layout(widths(1e9), overlap, B)[2] < B - 1:
+        raise ValueError("max_width too small to cover the range with this many windows")
+    while _layout(widths(b), overlap, B)[2] < B - 1:
+        b *= 2.0
     for _ in range(200):
         s = 0.5 * (a + b)
-        _, _, top = _layout(np.maximum(rel * s, min_width), overlap, B)
+        _, _, top = _layout(widths(s), overlap, B)
         if top >= B - 1:
             b = s
         else:
             a = s
-    nlo, nhi, _ = _layout(np.maximum(rel * b, min_width), overlap, B)
+    nlo, nhi, _ = _layout(widths(b), overlap, B)
     nhi[-1] = B - 1                              # the last window ends at the last bin
     if nhi[-1] - nlo[-1] + 1 < min_width:
         nlo[-1] = B - min_width

@@ -35,6 +35,21 @@ def test_slow_windows_get_narrower():
     assert pred[:-1].max() / pred[:-1].min() < 0.25 * t.max() / t.min()
 
 
+def test_width_cap():
+    """A cap keeps the widest window (and so every walker's shared-memory row)
+    bounded; the set still covers the range and stays valid."""
+    B, h, o = 16385, 64, 0.75                     # Ising L = 128, 64 windows
+    lo, hi = WN.equal_windows(B, h, o)
+    t = 1.0 + 100.0 * np.abs(np.linspace(-1, 1, h)) ** 2  # slow at both ends, fast in the middle
+    free_lo, free_hi = WN.balanced_windows(lo, hi, t, B, o, 5)
+    cap = 2 * int((hi - lo + 1)[0])
+    c_lo, c_hi = WN.balanced_windows(lo, hi, t, B, o, 5, max_width=cap)
+    assert (free_hi - free_lo + 1).max() > cap
+    assert WN.valid_windows(c_lo, c_hi, B, 5) and (c_hi - c_lo + 1).max() <= cap
+    with pytest.raises(ValueError):
+        WN.balanced_windows(lo, hi, t, B, o, 5, max_width=20)
+
+
 def test_invalid_sets_are_detected():
     assert not WN.valid_windows([0, 10, 20], [15, 25, 40], 42, 5)      # does not end at B - 1
     assert not WN.valid_windows([0, 16, 20], [15, 25, 41], 42, 5)      # gap
