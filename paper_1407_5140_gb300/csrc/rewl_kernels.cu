@@ -340,7 +340,6 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
     const int nw = n_win * m;
     const int tid = threadIdx.x, nthreads = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int n_prod = nthreads - 32;
     const bool consumer = warp == 0;
     const bool valid = consumer && lane < nw;
     const int tv = (consumer && lane < nw) ? lane : 0;
