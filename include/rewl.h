@@ -141,6 +141,20 @@ rewl_status rewl_run_to_convergence(rewl_ctx *ctx, long exchange_interval, long 
 rewl_status rewl_get_dos(rewl_ctx *ctx, int inst, double *ln_g, long cap, long *n_written,
                          long *e_of_bin, int per_window);
 
+/* The joining of rewl_get_dos (Sec. II B) applied to pieces the caller
+ * supplies, e.g. means of pieces over independent runs, or bootstrap
+ * resamples of them (Sec. II B, last paragraph).  Host-only: needs no context
+ * and no GPU.  h windows; pieces: h rows of w doubles, window i's bins
+ * lo[i] .. lo[i] + ww[i] - 1 at the start of row i; reach: B flags (1 =
+ * realisable energy); bin_width: energy per bin (4 Ising, 1 Potts); the result
+ * (B doubles, NaN on unrealisable bins) is shifted so the first realisable bin
+ * holds ln_g_first (ln 2 Ising, ln q Potts).  The windows must cover bins
+ * 0 .. B - 1, overlap their neighbours with increasing ends and be at least 5
+ * bins wide (REWL_EINVAL otherwise, message in rewl_last_error(NULL)). */
+rewl_status rewl_join_pieces(int h, int w, int B, const int32_t *lo, const int32_t *ww,
+                             const uint8_t *reach, double bin_width, double ln_g_first,
+                             const double *pieces, double *ln_g);
+
 /* Progress: all_converged over all instances; sweeps done; ln f per window of
  * instance `inst` (h values, 0 once converged; may be NULL). */
 rewl_status rewl_status_query(rewl_ctx *ctx, int inst, int *all_converged, double *ln_f_per_window,
@@ -252,9 +266,12 @@ void rewl_mlp_destroy(rewl_mlp *net);
  * otherwise, message in rewl_mlp_last_error(NULL)).  The activations live in a
  * static device array of 3,276,800 bytes that every GPU loading the library
  * holds until exit; the first call on a device looks up its address there (so
- * make that first call before any stream capture).  All calls share the
- * array: calls whose work overlaps on the GPU race.  Asynchronous on
- * cuda_stream (NULL: the legacy default stream); calls no allocator. */
+ * make that first call before any stream capture) and keeps it for the rest of
+ * the process: after cudaDeviceReset() on that device the kept address is
+ * stale, so the entry point must not be called again in that process.  All
+ * calls share the array: calls whose work overlaps on the GPU race.
+ * Asynchronous on cuda_stream (NULL: the legacy default stream); calls no
+ * allocator. */
 rewl_status rewl_mlp_forward_noalloc(const float *params, const float *x, float *y, int n, void *cuda_stream);
 
 /* Warm start of instance `inst`: every walker of window i gets

@@ -435,7 +435,7 @@ void rewl::plan_class(rewl_ctx *ctx, int ci, int wpc, int producers)
     c.sl.n_items = (int)c.items.size();
     c.sl.producers = producers;
     c.sl.threads = 32 * (1 + producers);
-    c.sl.smem = sweep_smem_bytes(nw, wpc, c.w, c.lat_words);
+    c.sl.smem = sweep_smem_bytes(nw, wpc, c.w, c.lat_words, producers, c.N);
     c.sl.max_walkers = nw;
     c.sl.max_w = c.w;
     c.sl.max_lat_words = c.lat_words;
@@ -841,30 +841,30 @@ extern "C" rewl_status rewl_status_query(rewl_ctx *ctx, int inst, int *all_conve
 }
 
 // Sec. II B: join the pieces where their five-point inverse-temperature
-// estimates agree best, above the previous join; normalise at the first bin.
-static void join_pieces(const HostInst &h, const std::vector<double> &pieces, std::vector<double> &out)
+// estimates agree best, above the previous join; normalise at the first
+// realisable bin to ln_min.  pieces: h rows of w values (window i's bins
+// lo[i] .. lo[i] + ww[i] - 1 first in its row).
+static void join_geometry(int H, int w, int B, const int *lo, const int *ww, const uint8_t *reach, double dE,
+                          double ln_min, const double *pieces, double *out)
 {
-    const InstDev &I = h.dev;
-    const int w = I.w, H = I.h, B = I.B, s = 1;
-    const double dE = I.step;
-    out.assign(B, NAN);
-    auto piece = [&](int i, int b) { return pieces[(size_t)i * w + (b - h.lo[i])]; };
-    const std::vector<int> &ww = h.ww;
+    const int s = 1;
+    for (int b = 0; b < B; ++b) out[b] = NAN;
+    auto piece = [&](int i, int b) { return pieces[(size_t)i * w + (b - lo[i])]; };
     auto beta = [&](int i, int b) {
         return (piece(i, b - 2 * s) - 8.0 * piece(i, b - s) + 8.0 * piece(i, b + s) - piece(i, b + 2 * s)) /
                (12.0 * s * dE);
     };
     double shift = 0.0;
-    int start = h.lo[0];
+    int start = lo[0];
     for (int i = 0; i + 1 < H; ++i) {
-        const int ov_lo = std::max(h.lo[i], h.lo[i + 1]);
-        const int ov_hi = std::min(h.lo[i] + ww[i] - 1, h.lo[i + 1] + ww[i + 1] - 1);
+        const int ov_lo = std::max(lo[i], lo[i + 1]);
+        const int ov_hi = std::min(lo[i] + ww[i] - 1, lo[i + 1] + ww[i + 1] - 1);
         int best = -1;
         double best_d = 0.0;
         for (int b = std::max(ov_lo, start + 1); b <= ov_hi; ++b) {
             if (b - 2 * s < ov_lo || b + 2 * s > ov_hi) continue;
             bool ok = true;
-            for (int d = -2; d <= 2; ++d) ok = ok && h.reach[b + d * s];
+            for (int d = -2; d <= 2; ++d) ok = ok && reach[b + d * s];
             if (!ok) continue;
             const double dd = std::fabs(beta(i, b) - beta(i + 1, b));
             if (best < 0 || dd < best_d) {
@@ -874,21 +874,51 @@ static void join_pieces(const HostInst &h, const std::vector<double> &pieces, st
         }
         if (best < 0) {
             best = std::max(ov_lo, start + 1);
-            while (best < ov_hi && !h.reach[best]) ++best;
+            while (best < ov_hi && !reach[best]) ++best;
         }
         for (int b = start; b < best; ++b) out[b] = piece(i, b) + shift;
         shift = piece(i, best) + shift - piece(i + 1, best);
         start = best;
     }
-    for (int b = start; b < h.lo[H - 1] + ww[H - 1]; ++b) out[b] = piece(H - 1, b) + shift;
+    for (int b = start; b < lo[H - 1] + ww[H - 1]; ++b) out[b] = piece(H - 1, b) + shift;
     int first = -1;
     for (int b = 0; b < B; ++b) {
-        if (!h.reach[b]) out[b] = NAN;
+        if (!reach[b]) out[b] = NAN;
         else if (first < 0) first = b;
     }
-    const double ln_min = std::log(I.model == REWL_ISING ? 2.0 : (double)I.q);
     const double off = ln_min - out[first];
     for (int b = 0; b < B; ++b) out[b] += off;
+}
+
+static void join_pieces(const HostInst &h, const std::vector<double> &pieces, std::vector<double> &out)
+{
+    const InstDev &I = h.dev;
+    out.assign(I.B, NAN);
+    join_geometry(I.h, I.w, I.B, h.lo.data(), h.ww.data(), h.reach.data(), (double)I.step,
+                  std::log(I.model == REWL_ISING ? 2.0 : (double)I.q), pieces.data(), out.data());
+}
+
+extern "C" rewl_status rewl_join_pieces(int h, int w, int B, const int32_t *lo, const int32_t *ww,
+                                        const uint8_t *reach, double bin_width, double ln_g_first,
+                                        const double *pieces, double *ln_g)
+{
+    if (h < 1 || w < 5 || B < 1 || !lo || !ww || !reach || !pieces || !ln_g || !(bin_width > 0.0))
+        return fail(nullptr, REWL_EINVAL, "rewl_join_pieces: bad argument");
+    if (lo[0] != 0 || lo[h - 1] + ww[h - 1] != B)
+        return fail(nullptr, REWL_EINVAL, "rewl_join_pieces: windows must cover bins 0 .. B - 1");
+    for (int i = 0; i < h; ++i) {
+        if (ww[i] < 5 || ww[i] > w || lo[i] < 0 || lo[i] + ww[i] > B)
+            return fail(nullptr, REWL_EINVAL, "rewl_join_pieces: window " + std::to_string(i) + " out of range");
+        if (i + 1 < h && (lo[i + 1] <= lo[i] || lo[i + 1] > lo[i] + ww[i] - 1 || lo[i + 1] + ww[i + 1] <= lo[i] + ww[i]))
+            return fail(nullptr, REWL_EINVAL, "rewl_join_pieces: windows " + std::to_string(i) + " and " +
+                                                  std::to_string(i + 1) + " must overlap with increasing ends");
+    }
+    bool any = false;
+    for (int b = 0; b < B; ++b) any = any || reach[b];
+    if (!any) return fail(nullptr, REWL_EINVAL, "rewl_join_pieces: no realisable bin");
+    std::vector<int> vlo(lo, lo + h), vww(ww, ww + h);
+    join_geometry(h, w, B, vlo.data(), vww.data(), reach, bin_width, ln_g_first, pieces, ln_g);
+    return REWL_OK;
 }
 
 extern "C" rewl_status rewl_get_dos(rewl_ctx *ctx, int inst, double *ln_g, long cap, long *n_written,

@@ -111,7 +111,7 @@ int launch_sweeps(const DevState &st, const SweepLaunch &sl, long n_sweeps, long
 int launch_exchange(const DevState &st, const ExTask *tasks0, int n0, const ExTask *tasks1, int n1,
                     void *stream);
 int launch_bump(const DevState &st, long sweeps, long exchanges, void *stream);
-int sweep_smem_bytes(int n_walkers, int n_win, int w, int lat_words);
+int sweep_smem_bytes(int n_walkers, int n_win, int w, int lat_words, int producers, int N);
 int prepare_sweep(int model, int producers, int smem);
 int launch_debug_lam(const uint32_t *k, int64_t *out, long n, void *stream);
 int launch_debug_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr, uint32_t *out, long n,

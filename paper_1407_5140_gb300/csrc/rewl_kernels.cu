@@ -124,8 +124,10 @@ static constexpr int kR = 32;
 // the bins b-4..b+4 speculatively before it knows the energy change.
 static constexpr int kGuard = 4;
 
-int sweep_smem_bytes(int n_walkers, int n_win, int w, int lat_words)
+int sweep_smem_bytes(int n_walkers, int n_win, int w, int lat_words, int producers, int N)
 {
+    (void)producers;
+    (void)N;
     long long b = 0;
     b += 2LL * n_walkers * kR * 48;                     // trial ring, 2 slots (48-byte records)
     b += (long long)n_walkers * (w + 2 * kGuard) * 8;   // ln g with guards

@@ -41,11 +41,18 @@ static_assert(kNParams == 33921, "parameter count");
 
 typedef __nv_bfloat16 bf16;
 
+// Reductions over samples are split in at most kMaxParts pieces; their partial
+// sums (at most kMaxParts x 128 x 128 floats) are added in a fixed order.
+static constexpr int kMaxParts = 32;
+static constexpr size_t kPartFloats = (size_t)kMaxParts * kH * kH;
+
 // ---------------------------------------------------------------------------
 // tensor-core GEMM: C[M x N] = A[M x K] * Bn[N x K]^T, A and Bn K-contiguous
 // BF16, FP32 accumulation.  A block of 4 warps computes a 64 x 64 tile; warp
 // w owns rows 16w..16w+15 and all 64 columns (8 mma n-tiles).  blockIdx.z
-// splits K (partial sums reduced by atomics in the gradient epilogue).
+// splits K: the gradient epilogue stores each split's partial tile, and a
+// second kernel adds the splits in a fixed order (no float atomics, so every
+// gradient and training run is bitwise repeatable).
 // Fragment layout of mma.m16n8k16.row.col (PTX ISA): lane = 4 g + c;
 // A regs {(g, 2c..2c+1), (g+8, 2c..), (g, 2c+8..), (g+8, 2c+8..)};
 // B regs {(k = 2c.., n = g), (k = 2c+8.., n = g)}; C {(g, 2c), (g, 2c+1),
@@ -54,7 +61,7 @@ typedef __nv_bfloat16 bf16;
 enum Epi : int {
     kEpiForward = 0,   // z = acc + bias; h = tanh(z): H f32, Hb bf16 [M x N], HTb bf16 [N x M]
     kEpiBackward = 1,  // dz = acc * (1 - Hprev^2): dZ f32, dZb bf16, dZTb bf16
-    kEpiGrad = 2       // atomicAdd(G[m][n], acc)
+    kEpiGrad = 2       // G[split][m][n] = acc (partial sums, added by reduce_parts_kernel)
 };
 
 struct GemmArgs {
@@ -125,7 +132,7 @@ __global__ void __launch_bounds__(128) gemm_kernel(GemmArgs g)
                 g.out_b[mn] = __float2bfloat16_rn(dz);
                 g.out_bt[nm] = __float2bfloat16_rn(dz);
             } else {
-                atomicAdd(g.out_f + mn, v);
+                g.out_f[(size_t)blockIdx.z * g.M * g.N + mn] = v;
             }
         }
     }
@@ -149,9 +156,10 @@ __global__ void layer1_kernel(const float *x, const float *p, int n, float *H, b
     HTb[(size_t)u * n + s] = __float2bfloat16_rn(h);
 }
 
-// y = W4 h3 + b4; with targets: dy = (y - t) / n, loss += (y - t)^2 / (2 n)
+// y = W4 h3 + b4; with targets: dy = (y - t) / n and the sample's loss term
+// lterm = (y - t)^2 / (2 n) (summed by sum_kernel)
 __global__ void output_kernel(const float *H3, const float *p, int n, float *y, const float *t, float *dy,
-                              float *loss)
+                              float *lterm)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -161,7 +169,7 @@ __global__ void output_kernel(const float *H3, const float *p, int n, float *y, 
     if (t) {
         const float d = z - t[s];
         dy[s] = d / (float)n;
-        atomicAdd(loss, 0.5f * d * d / (float)n);
+        lterm[s] = 0.5f * d * d / (float)n;
     }
 }
 
@@ -178,19 +186,19 @@ __global__ void back3_kernel(const float *dy, const float *H3, const float *p, i
     dZTb[(size_t)u * n + s] = __float2bfloat16_rn(dz);
 }
 
-// out[u] += sum_s w[s] X[s][u] (w = NULL: weights 1); one block of 128
-// threads per chunk of rows
-__global__ void colsum_kernel(const float *X, const float *w, int n, int rows_per_block, float *out)
+// part[block][u] = sum over the block's rows s of w[s] X[s][u] (w = NULL:
+// weights 1); one block of 128 threads per chunk of rows
+__global__ void colsum_kernel(const float *X, const float *w, int n, int rows_per_block, float *part)
 {
     const int u = threadIdx.x;
     const int s0 = blockIdx.x * rows_per_block, s1 = min(n, s0 + rows_per_block);
     float acc = 0.f;
     for (int s = s0; s < s1; ++s) acc += (w ? w[s] : 1.f) * X[(size_t)s * kH + u];
-    atomicAdd(out + u, acc);
+    part[(size_t)blockIdx.x * kH + u] = acc;
 }
 
-// dW1[u][k] += sum_s dZ1[s][u] x[s][k]
-__global__ void dw1_kernel(const float *dZ1, const float *x, int n, int rows_per_block, float *g)
+// part[block][u][k] = sum over the block's rows s of dZ1[s][u] x[s][k]
+__global__ void dw1_kernel(const float *dZ1, const float *x, int n, int rows_per_block, float *part)
 {
     const int u = threadIdx.x;
     const int s0 = blockIdx.x * rows_per_block, s1 = min(n, s0 + rows_per_block);
@@ -201,7 +209,17 @@ __global__ void dw1_kernel(const float *dZ1, const float *x, int n, int rows_per
         for (int k = 0; k < kIn; ++k) acc[k] = fmaf(d, x[s * kIn + k], acc[k]);
     }
 #pragma unroll
-    for (int k = 0; k < kIn; ++k) atomicAdd(g + kOffW1 + u * kIn + k, acc[k]);
+    for (int k = 0; k < kIn; ++k) part[(size_t)blockIdx.x * kH * kIn + u * kIn + k] = acc[k];
+}
+
+// out[i] = sum over p = 0, 1, ... of part[p][i], in that order
+__global__ void reduce_parts_kernel(const float *part, int n_parts, int len, float *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    float acc = 0.f;
+    for (int p = 0; p < n_parts; ++p) acc += part[(size_t)p * len + i];
+    out[i] = acc;
 }
 
 // BF16 copies of W2, W3 and of their transposes
@@ -238,6 +256,22 @@ __global__ void init_params_kernel(float *p, uint32_t k0, uint32_t k1)
     const float fan = i < kOffW2 ? (float)kIn : (i < kOffW4 ? (float)kH : (float)kH);
     const float a = rsqrtf(fan);
     p[i] = a * (2.f * ((float)(r.x >> 8) * (1.f / 16777216.f)) - 1.f);
+}
+
+// *out = sum of v[0..n) (db4, the loss): one block of 256 threads, each
+// thread's strided sum, then a fixed reduction tree
+__global__ void sum_kernel(const float *v, int n, float *out)
+{
+    __shared__ float red[256];
+    float acc = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += v[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -316,6 +350,8 @@ struct rewl_mlp {
     // activations and gradients of one batch (scratch)
     float *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *dZ = nullptr, *dZ1 = nullptr, *y = nullptr, *dy = nullptr,
           *loss = nullptr, *xbuf = nullptr, *sbuf = nullptr;
+    float *lterm = nullptr;   // per-sample loss terms
+    float *part = nullptr;    // partial sums of the gradient reductions (kPartFloats)
     bf16 *H1b = nullptr, *H2b = nullptr, *H1Tb = nullptr, *H2Tb = nullptr, *dZb = nullptr, *dZTb = nullptr;
     long step = 0;
     long launches = 0;
@@ -349,7 +385,7 @@ extern "C" void rewl_mlp_destroy(rewl_mlp *net)
     if (net->stream) cudaStreamSynchronize(net->stream);
     void *bufs[] = {net->p, net->m, net->v, net->g, net->W2b, net->W3b, net->W2Tb, net->W3Tb, net->H1, net->H2, net->H3,
                     net->dZ, net->dZ1, net->y, net->dy, net->loss, net->xbuf, net->sbuf, net->H1b, net->H2b,
-                    net->H1Tb, net->H2Tb, net->dZb, net->dZTb};
+                    net->H1Tb, net->H2Tb, net->dZb, net->dZTb, net->lterm, net->part};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (net->own_stream && net->stream) cudaStreamDestroy(net->stream);
@@ -387,6 +423,8 @@ extern "C" rewl_status rewl_mlp_create(rewl_mlp **out, int max_batch, unsigned l
     MCK(malloc_n(&net->loss, 1));
     MCK(malloc_n(&net->xbuf, B * kIn));
     MCK(malloc_n(&net->sbuf, B));
+    MCK(malloc_n(&net->lterm, B));
+    MCK(malloc_n(&net->part, (size_t)kPartFloats));
     MCK(malloc_n(&net->H1b, HB));
     MCK(malloc_n(&net->H2b, HB));
     MCK(malloc_n(&net->H1Tb, HB));
@@ -462,36 +500,36 @@ static rewl_status forward(rewl_mlp *net, const float *x, int n, float *y, const
     a.out_b = net->dZb;
     a.out_bt = net->dZTb;
     if ((s = run_gemm(net, kEpiForward, a, 1))) return s;
-    if (t) MCK(cudaMemsetAsync(net->loss, 0, 4, net->stream));
-    output_kernel<<<(n + 127) / 128, 128, 0, net->stream>>>(net->H3, net->p, n, y, t, net->dy, net->loss);
+    output_kernel<<<(n + 127) / 128, 128, 0, net->stream>>>(net->H3, net->p, n, y, t, net->dy, net->lterm);
     net->launches += 1;
+    if (t) {
+        sum_kernel<<<1, 256, 0, net->stream>>>(net->lterm, n, net->loss);
+        net->launches += 1;
+    }
     MCK(cudaGetLastError());
     return REWL_OK;
 }
 
-// db4 = sum dy (one scalar)
-__global__ void sum_kernel(const float *v, int n, float *out)
-{
-    float acc = 0.f;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += v[i];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
-}
 
-// Gradient of the loss into net->g (zeroed first), after forward() with
-// targets.  Buffer use: dZ3 in dZ/dZb/dZTb; dZ2 in dZ (f32) and in the H2
-// bf16 buffers (H2b, H2Tb are dead once dW3 is formed); dZ1 in dZ1.
+// Gradient of the loss into net->g, after forward() with targets.  Buffer
+// use: dZ3 in dZ/dZb/dZTb; dZ2 in dZ (f32) and in the H2 bf16 buffers (H2b,
+// H2Tb are dead once dW3 is formed); dZ1 in dZ1.  Every sum over samples is
+// formed as at most kMaxParts partial sums in net->part, then added in order.
 static rewl_status backward(rewl_mlp *net, const float *x, int n)
 {
     rewl_status s;
-    MCK(cudaMemsetAsync(net->g, 0, kNParams * 4, net->stream));
-    const int rpb = 256;
-    const int nb = (n + rpb - 1) / rpb;
-    const int splits = std::max(1, std::min(32, n / 512));
+    const int rpb = (n + kMaxParts - 1) / kMaxParts;   // rows per colsum / dw1 block
+    const int nb = (n + rpb - 1) / rpb;                 // <= kMaxParts
+    const int splits = std::max(1, std::min(kMaxParts, n / 512));
     const int kc = ((n / splits + 15) / 16) * 16;
-    const int ksplits = (n + kc - 1) / kc;
+    const int ksplits = (n + kc - 1) / kc;              // <= splits
+    auto reduce = [&](int parts, int len, float *out) {
+        reduce_parts_kernel<<<(len + 255) / 256, 256, 0, net->stream>>>(net->part, parts, len, out);
+        net->launches += 1;
+    };
     // layer 4: dW4 = sum_s dy h3, db4 = sum_s dy
-    colsum_kernel<<<nb, kH, 0, net->stream>>>(net->H3, net->dy, n, rpb, net->g + kOffW4);
+    colsum_kernel<<<nb, kH, 0, net->stream>>>(net->H3, net->dy, n, rpb, net->part);
+    reduce(nb, kH, net->g + kOffW4);
     sum_kernel<<<1, 256, 0, net->stream>>>(net->dy, n, net->g + kOffB4);
     // dZ3 = dy W4 (1 - h3^2)
     back3_kernel<<<(n * kH + 255) / 256, 256, 0, net->stream>>>(net->dy, net->H3, net->p, n, net->dZ, net->dZb,
@@ -505,9 +543,11 @@ static rewl_status backward(rewl_mlp *net, const float *x, int n)
     a.N = kH;
     a.K = n;
     a.k_chunk = kc;
-    a.out_f = net->g + kOffW3;
+    a.out_f = net->part;
     if ((s = run_gemm(net, kEpiGrad, a, ksplits))) return s;
-    colsum_kernel<<<nb, kH, 0, net->stream>>>(net->dZ, nullptr, n, rpb, net->g + kOffB3);
+    reduce(ksplits, kH * kH, net->g + kOffW3);
+    colsum_kernel<<<nb, kH, 0, net->stream>>>(net->dZ, nullptr, n, rpb, net->part);
+    reduce(nb, kH, net->g + kOffB3);
     net->launches += 1;
     // dZ2 = (dZ3 W3) (1 - h2^2)
     GemmArgs b{};
@@ -525,9 +565,10 @@ static rewl_status backward(rewl_mlp *net, const float *x, int n)
     // layer 2: dW2 = dZ2^T H1, db2 = sum dZ2
     a.A = net->H2Tb;
     a.Bn = net->H1Tb;
-    a.out_f = net->g + kOffW2;
     if ((s = run_gemm(net, kEpiGrad, a, ksplits))) return s;
-    colsum_kernel<<<nb, kH, 0, net->stream>>>(net->dZ, nullptr, n, rpb, net->g + kOffB2);
+    reduce(ksplits, kH * kH, net->g + kOffW2);
+    colsum_kernel<<<nb, kH, 0, net->stream>>>(net->dZ, nullptr, n, rpb, net->part);
+    reduce(nb, kH, net->g + kOffB2);
     net->launches += 1;
     // dZ1 = (dZ2 W2) (1 - h1^2)
     b.A = net->H2b;
@@ -538,8 +579,10 @@ static rewl_status backward(rewl_mlp *net, const float *x, int n)
     b.out_bt = net->dZTb;
     if ((s = run_gemm(net, kEpiBackward, b, 1))) return s;
     // layer 1: dW1 = dZ1^T x, db1 = sum dZ1
-    dw1_kernel<<<nb, kH, 0, net->stream>>>(net->dZ1, x, n, rpb, net->g);
-    colsum_kernel<<<nb, kH, 0, net->stream>>>(net->dZ1, nullptr, n, rpb, net->g + kOffB1);
+    dw1_kernel<<<nb, kH, 0, net->stream>>>(net->dZ1, x, n, rpb, net->part);
+    reduce(nb, kH * kIn, net->g + kOffW1);
+    colsum_kernel<<<nb, kH, 0, net->stream>>>(net->dZ1, nullptr, n, rpb, net->part);
+    reduce(nb, kH, net->g + kOffB1);
     net->launches += 2;
     MCK(cudaGetLastError());
     return REWL_OK;
@@ -583,7 +626,10 @@ extern "C" rewl_status rewl_mlp_train_step(rewl_mlp *net, const float *x_dev, co
     if ((s = forward(net, x_dev, n, nullptr, t_dev))) return s;
     if ((s = backward(net, x_dev, n))) return s;
     net->step += 1;
-    const float c1 = 1.f - powf(0.9f, (float)net->step), c2 = 1.f - powf(0.999f, (float)net->step);
+    // bias corrections 1 - beta^t in double: in FP32, 1 - 0.999^t loses most
+    // of its digits to cancellation for small t
+    const float c1 = (float)(1.0 - std::pow(0.9, (double)net->step));
+    const float c2 = (float)(1.0 - std::pow(0.999, (double)net->step));
     adam_kernel<<<(kNParams + 255) / 256, 256, 0, net->stream>>>(net->p, net->m, net->v, net->g, kNParams, lr, c1, c2);
     net->launches += 1;
     MCK(cudaGetLastError());

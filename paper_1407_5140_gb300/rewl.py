@@ -82,6 +82,7 @@ def lib():
         L.rewl_mlp_destroy.restype = None
         L.rewl_warm_start.argtypes = [vp, i32, vp, f64]
         L.rewl_mlp_forward_noalloc.argtypes = [vp, vp, vp, i32, vp]
+        L.rewl_join_pieces.argtypes = [i32, i32, i32, vp, vp, vp, f64, f64, vp, vp]
         L.rewl_debug_lam.argtypes = [vp, vp, i64]
         L.rewl_debug_philox.argtypes = [u32, u32, vp, vp, i64]
         for name in ("rewl_create", "rewl_create_batch", "rewl_run", "rewl_exchange", "rewl_run_cycles",
@@ -89,7 +90,7 @@ def lib():
                      "rewl_geometry", "rewl_get_state", "rewl_get_counters", "rewl_set_option", "rewl_save",
                      "rewl_load", "rewl_debug_lam", "rewl_debug_philox", "rewl_mlp_create", "rewl_mlp_set_params",
                      "rewl_mlp_get_params", "rewl_mlp_forward", "rewl_mlp_gradient", "rewl_mlp_train_step",
-                     "rewl_warm_start", "rewl_mlp_forward_noalloc"):
+                     "rewl_warm_start", "rewl_mlp_forward_noalloc", "rewl_join_pieces"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -291,6 +292,23 @@ class Rewl:
         return out, e
 
 
+def join_pieces(pieces, lo, ww, reach, bin_width, ln_g_first):
+    """rewl_join_pieces: join per-window ln g pieces (h x w array, window i's
+    bins lo[i] .. lo[i] + ww[i] - 1 first in row i) as rewl_get_dos does
+    (Sec. II B); host only.  Returns B values, NaN on unrealisable bins."""
+    P = np.ascontiguousarray(pieces, np.float64)
+    h, w = P.shape
+    lo = np.ascontiguousarray(lo, np.int32)
+    ww = np.ascontiguousarray(np.broadcast_to(np.asarray(ww, np.int32), (h,)), np.int32)
+    reach = np.ascontiguousarray(reach, np.uint8)
+    out = np.zeros(reach.size, np.float64)
+    code = lib().rewl_join_pieces(h, w, reach.size, _p(lo), _p(ww), _p(reach), float(bin_width), float(ln_g_first),
+                                  _p(P), _p(out))
+    if code != 0:
+        raise RewlError(code, lib().rewl_last_error(None).decode())
+    return out
+
+
 # -- primitive checks (device pointers from torch tensors)
 def debug_lam(k_dev, out_dev, n):
     _check(lib().rewl_debug_lam(C.c_void_p(k_dev), C.c_void_p(out_dev), n))
@@ -344,19 +362,24 @@ class Mlp:
         return a
 
     def forward(self, x, y):
-        _mcheck(lib().rewl_mlp_forward(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.shape[0]),
-                self._h)
+        n = _check_rows(x, 5, "x")
+        _check_vec(y, n, "y")
+        _mcheck(lib().rewl_mlp_forward(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), n), self._h)
 
     def gradient(self, x, t):
+        n = _check_rows(x, 5, "x")
+        _check_vec(t, n, "t")
         g = np.zeros(N_PARAMS, np.float32)
         loss = np.zeros(1, np.float32)
-        _mcheck(lib().rewl_mlp_gradient(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()), x.shape[0],
+        _mcheck(lib().rewl_mlp_gradient(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()), n,
                                         _p(g), _p(loss)), self._h)
         return g, float(loss[0])
 
     def train_step(self, x, t, lr, want_loss=False):
+        n = _check_rows(x, 5, "x")
+        _check_vec(t, n, "t")
         loss = np.zeros(1, np.float32)
-        _mcheck(lib().rewl_mlp_train_step(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()), x.shape[0],
+        _mcheck(lib().rewl_mlp_train_step(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()), n,
                                           lr, _p(loss) if want_loss else None), self._h)
         return float(loss[0]) if want_loss else None
 
@@ -364,10 +387,42 @@ class Mlp:
         return int(lib().rewl_mlp_launch_count(self._h))
 
 
+def _check_dev_f32(a, name):
+    """a must be a contiguous float32 CUDA tensor on the current device: the
+    kernels read and write it through its raw pointer."""
+    import torch
+    if not isinstance(a, torch.Tensor):
+        raise ValueError(f"{name} must be a torch tensor")
+    if a.dtype != torch.float32 or not a.is_cuda or not a.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if a.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on cuda:{a.device.index}, the current device is cuda:{torch.cuda.current_device()}")
+
+
+def _check_rows(x, cols, name):
+    _check_dev_f32(x, name)
+    if x.dim() != 2 or x.shape[1] != cols:
+        raise ValueError(f"{name} must have shape [n, {cols}]")
+    return int(x.shape[0])
+
+
+def _check_vec(v, n, name):
+    _check_dev_f32(v, name)
+    if v.numel() < n:
+        raise ValueError(f"{name} holds {v.numel()} values, {n} needed")
+
+
 def mlp_forward_noalloc(params, x, y, stream=None):
     """rewl_mlp_forward_noalloc: network output without any device allocation.
-    params (33921 floats), x ([n, 5]) and y ([n]) are float32 CUDA tensors."""
+    params (33921 floats), x ([n, 5]) and y ([n]) are contiguous float32 CUDA
+    tensors on the current device; anything else raises ValueError before the
+    library is called."""
+    n = _check_rows(x, 5, "x")
+    _check_vec(y, n, "y")
+    _check_dev_f32(params, "params")
+    if params.numel() != N_PARAMS:
+        raise ValueError(f"params must hold {N_PARAMS} values")
     code = lib().rewl_mlp_forward_noalloc(C.c_void_p(params.data_ptr()), C.c_void_p(x.data_ptr()),
-                                          C.c_void_p(y.data_ptr()), x.shape[0], _stream_ptr(stream))
+                                          C.c_void_p(y.data_ptr()), n, _stream_ptr(stream))
     if code != 0:
         raise RewlError(code, lib().rewl_mlp_last_error(None).decode())

@@ -1,5 +1,7 @@
 """Canonical thermodynamics from a density of states, peak finding, bootstrap
-errors over independent runs and the finite-size extrapolation of a
+errors over independent runs (of a scalar, and of the joined DOS by
+resampling the pieces of every window, Sec. II B) and the finite-size
+extrapolation of a
 transition temperature (Sec. III and Sec. IV A: the q = 10 Potts transition
 located from the specific-heat maxima of L x L lattices).
 
@@ -83,6 +85,33 @@ def bootstrap(samples, stat=np.mean, n_resamples=200, seed=0):
     n = x.shape[0]
     reps = np.array([stat(x[rng.integers(0, n, n)]) for _ in range(n_resamples)])
     return stat(x), float(np.std(reps, ddof=1))
+
+
+def bootstrap_dos(pieces, lo, ww, reach, bin_width, ln_g_first, n_resamples=200, seed=0, observables=None):
+    """Error analysis of Sec. II B (last paragraph) over n independent runs of
+    one instance.  pieces: (n, h, w) per-window ln g of every run.  The mean of
+    the n pieces of each window, joined, is the mean global DOS; each bootstrap
+    resample draws n pieces with replacement for every window separately,
+    averages them and joins the result, so the join points differ between
+    resamples.  Returns (mean_ln_g, std_ln_g over the resamples, and for each
+    observables[name](ln_g) the value on the mean DOS with its standard error).
+    The joining is the library's (rewl_join_pieces)."""
+    from . import rewl as R
+    P = np.asarray(pieces, np.float64)
+    n, h, w = P.shape
+    mean = R.join_pieces(P.mean(axis=0), lo, ww, reach, bin_width, ln_g_first)
+    rng = np.random.default_rng(seed)
+    reps = np.empty((n_resamples, mean.size))
+    obs = {k: [] for k in (observables or {})}
+    for r in range(n_resamples):
+        pick = rng.integers(0, n, size=(h, n))                  # n runs per window, with repetition
+        res = P[pick, np.arange(h)[:, None], :].mean(axis=1)    # (h, w)
+        reps[r] = R.join_pieces(res, lo, ww, reach, bin_width, ln_g_first)
+        for k, f in (observables or {}).items():
+            obs[k].append(f(reps[r]))
+    std = np.std(reps, axis=0, ddof=1)
+    out_obs = {k: (f(mean), np.std(np.asarray(obs[k]), axis=0, ddof=1)) for k, f in (observables or {}).items()}
+    return mean, std, out_obs
 
 
 def extrapolate_tc(L, Tc, err=None, power=2):

@@ -56,13 +56,23 @@ def train(net, X, T, steps=3000, batch=4096, lr=2e-3, seed=0, log_every=0, lr_en
     rng = np.random.default_rng(seed)
     batch = min(batch, net.max_batch)
     batch -= batch % 64
-    Xd = torch.from_numpy(np.ascontiguousarray(X, np.float32)).cuda()
-    Td = torch.from_numpy(np.ascontiguousarray(T, np.float32)).cuda()
+    X = np.ascontiguousarray(X, np.float32)
+    T = np.ascontiguousarray(T, np.float32)
+    # mini-batches are gathered on the host into pinned buffers and copied in
+    xh = torch.empty((batch, 5), dtype=torch.float32).pin_memory()
+    th = torch.empty(batch, dtype=torch.float32).pin_memory()
+    xb = torch.empty((batch, 5), dtype=torch.float32, device="cuda")
+    tb = torch.empty(batch, dtype=torch.float32, device="cuda")
     hist = []
     for it in range(steps):
-        idx = torch.from_numpy(rng.integers(0, X.shape[0], batch)).cuda()
-        xb = Xd.index_select(0, idx).contiguous()
-        tb = Td.index_select(0, idx).contiguous()
+        idx = rng.integers(0, X.shape[0], batch)
+        # the previous step (on the network's stream) is done with xb, tb and
+        # its copies have left the pinned buffers
+        torch.cuda.synchronize()
+        np.take(X, idx, axis=0, out=xh.numpy())
+        np.take(T, idx, out=th.numpy())
+        xb.copy_(xh, non_blocking=True)
+        tb.copy_(th, non_blocking=True)
         want = bool(log_every) and (it % log_every == 0 or it == steps - 1)
         step_lr = lr if lr_end is None else lr_end + 0.5 * (lr - lr_end) * (1.0 + math.cos(math.pi * it / max(1, steps - 1)))
         loss = net.train_step(xb, tb, step_lr, want_loss=want)

@@ -471,7 +471,3 @@ def test_mlp_reference_gradient_matches_finite_differences():
         pm[i] -= h
         fd = (M.loss(pp, x, t) - M.loss(pm, x, t)) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(fd), (i, fd, g[i])
-    # one Adam step moves every parameter against its gradient
-    p2, m, v = M.adam_step(p, np.zeros_like(p), np.zeros_like(p), g, 1, 1e-3)
-    moved = np.sign(p - p2)[np.abs(g) > 1e-12]
-    assert np.all(moved == np.sign(g[np.abs(g) > 1e-12]))

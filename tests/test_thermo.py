@@ -90,3 +90,49 @@ def test_extrapolation_recovers_a_known_limit():
     tc, se, a = TH.extrapolate_tc(L, 0.7012316 + 0.83 / L ** 2 + np.array([1, -1, 1, -1, 1]) * 1e-4,
                                   err=np.full(5, 1e-4))
     assert abs(tc - 0.7012316) < 3 * se and 0.0 < se < 1e-3
+
+
+def test_bootstrap_dos_matches_the_spread_of_independent_experiments():
+    """Sec. II B error analysis on synthetic pieces with a known spread: the
+    exact Ising L = 8 DOS cut into 4 windows at 75 % overlap, every run's piece
+    shifted by its own arbitrary constant (as WL leaves it) plus independent
+    noise of sigma per bin.  The bootstrap standard error of the joined ln g
+    from one experiment of n runs must match the spread of the joined mean DOS
+    over many independent experiments, and the mean DOS must sit on the exact
+    one within that spread.  Runs through the library's host-only joining."""
+    from paper_1407_5140_gb300 import thermo as TH
+    from paper_1407_5140_gb300 import windows as WN
+    rows = np.loadtxt(os.path.join(GOLDEN, "ising_L8_exact_lng.txt"), usecols=(0, 1))
+    N, B = 64, 65
+    exact = np.full(B, np.nan)
+    exact[((rows[:, 0] + 2 * N) // 4).astype(int)] = rows[:, 1]
+    reach = np.isfinite(exact).astype(np.uint8)
+    lo, hi = WN.equal_windows(B, 4, 0.75)
+    w = int(hi[0] - lo[0] + 1)
+    base = np.nan_to_num(exact)
+    rng = np.random.default_rng(3)
+    n, sigma = 16, 0.02
+
+    def experiment():
+        P = np.empty((n, 4, w))
+        for r in range(n):
+            for i in range(4):
+                P[r, i] = base[lo[i]:lo[i] + w] + rng.uniform(-50, 50) + rng.normal(0, sigma, w)
+        return P
+
+    mean, std, obs = TH.bootstrap_dos(experiment(), lo, w, reach, 4.0, math.log(2), n_resamples=200, seed=1,
+                                      observables={"lnZ(T=3)": lambda lg: TH.log_z(lg, -2 * N + 4 * np.arange(B), 3.0)[0]})
+    from paper_1407_5140_gb300 import rewl as R
+    means = np.array([R.join_pieces(experiment().mean(axis=0), lo, w, reach, 4.0, math.log(2)) for _ in range(300)])
+    emp = np.std(means, axis=0, ddof=1)
+    ok = reach.astype(bool)
+    ok[0] = False                                   # fixed by the normalisation
+    ratio = std[ok] / emp[ok]
+    assert 0.7 < np.median(ratio) < 1.4, np.median(ratio)
+    assert np.all((ratio > 0.3) & (ratio < 3.0)), ratio
+    # the mean DOS is unbiased: within a few standard errors of the exact one
+    z = (mean[ok] - exact[ok]) / emp[ok]
+    assert np.max(np.abs(z)) < 5.0 and abs(np.mean(z)) < 1.0, (np.max(np.abs(z)), np.mean(z))
+    # an observable's error follows too
+    val, err = obs["lnZ(T=3)"]
+    assert err > 0 and np.isfinite(val)

@@ -5,13 +5,18 @@ rewl_mlp_forward_noalloc serves callers that must not allocate device memory
 while they run (device memory owned by another allocator, or no room for
 cudaMalloc's device-wide synchronisation where they call from): its
 activations live in a static device array, so it only needs the parameters,
-inputs and outputs the caller already has.  Two calls in a row -- with
+inputs and outputs the caller already has.  It launches the same kernels as
+the regular forward pass on the same inputs, so two calls in a row -- with
 different batches, so the second one finds the first one's leftovers in the
-shared scratch -- must each match the regular forward pass within the tolerance
-of the other network tests.  This file is collected last on purpose.
+shared scratch -- must each equal the regular pass bit for bit, and both must
+match the network's BF16-operand statement in oracle/mlp.py within the bound
+of the other network tests.  The file is collected last so that, if it fails,
+a run stopping at the first failure has run everything else.
 """
 import numpy as np
 import pytest
+
+from oracle import mlp as M
 
 pytestmark = pytest.mark.gpu
 
@@ -28,21 +33,23 @@ def test_noalloc_forward_matches_regular_forward_on_two_calls():
     from paper_1407_5140_gb300 import rewl as R
 
     stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
-    net = R.Mlp(max_batch=1024, seed=21, stream=stream)
-    params = torch.from_numpy(net.get_params()).cuda()
-    for call, n in enumerate((1024, 320)):
-        x = torch.from_numpy(_features(n, 100 + call)).cuda()
-        y_ref = torch.empty(n, dtype=torch.float32, device="cuda")
-        net.forward(x, y_ref)
-        y = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda")
-        R.mlp_forward_noalloc(params, x, y, stream=stream)
-        stream.synchronize()
-        a, b = y.cpu().numpy(), y_ref.cpu().numpy()
-        assert np.all(np.isfinite(a))
-        assert np.max(np.abs(a - b)) <= 2e-2 * np.max(np.abs(b)) + 2e-3, call
-    torch.cuda.synchronize()
-    net.close()
+    with torch.cuda.stream(stream):
+        net = R.Mlp(max_batch=1024, seed=21, stream=stream)
+        host_params = net.get_params()
+        params = torch.from_numpy(host_params).cuda()
+        for call, n in enumerate((1024, 320)):
+            xh = _features(n, 100 + call)
+            x = torch.from_numpy(xh).cuda()
+            y_ref = torch.empty(n, dtype=torch.float32, device="cuda")
+            net.forward(x, y_ref)
+            y = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda")
+            R.mlp_forward_noalloc(params, x, y, stream=stream)
+            stream.synchronize()
+            a, b = y.cpu().numpy(), y_ref.cpu().numpy()
+            assert np.array_equal(a, b), call
+            yb, _, ya = M.forward_bf16(host_params.astype(np.float64), xh.astype(np.float64))
+            assert np.all(np.abs(a.astype(np.float64) - yb) <= 4e-3 * ya), call
+        net.close()
 
 
 def test_noalloc_forward_rejects_batches_above_its_limit():
@@ -56,3 +63,12 @@ def test_noalloc_forward_rejects_batches_above_its_limit():
         with pytest.raises(R.RewlError) as ei:
             R.mlp_forward_noalloc(params, x, y)
         assert ei.value.code == -1
+    # malformed tensors never reach the library
+    x = torch.zeros((64, 5), dtype=torch.float32, device="cuda")
+    y = torch.zeros(64, dtype=torch.float32, device="cuda")
+    for bad in (dict(params=params[:-1]), dict(x=x.double()), dict(y=y[:32]), dict(x=x.t().contiguous().t()),
+                dict(x=x.cpu())):
+        args = dict(params=params, x=x, y=y)
+        args.update(bad)
+        with pytest.raises(ValueError):
+            R.mlp_forward_noalloc(args["params"], args["x"], args["y"])
