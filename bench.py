@@ -62,12 +62,16 @@ class ClockSampler:
         self.p = None
 
     def __enter__(self):
+        import tempfile
         vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
         idx = vis.split(",")[self.gpu] if vis and vis.split(",")[0].isdigit() else str(self.gpu)
+        # samples go to a file: a pipe nobody reads would fill and stall the
+        # sampler during long regions
+        self.f = tempfile.TemporaryFile(mode="w+")
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", idx, f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "200"],
-                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                                      stdout=self.f, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
         return self
@@ -77,9 +81,12 @@ class ClockSampler:
         if self.p:
             self.p.terminate()
             try:
-                self.out, _ = self.p.communicate(timeout=5)
+                self.p.wait(timeout=5)
             except Exception:
                 self.p.kill()
+        self.f.seek(0)
+        self.out = self.f.read()
+        self.f.close()
 
     def summary(self):
         rows = []
@@ -217,19 +224,18 @@ def run_ours(args, rank, world):
     # end to end through the public API: descriptors in (host), ln g out (host)
     t0 = time.perf_counter()
     e2e_ctx = R.Rewl([R.instance(**d) for d in ds], stream=stream)
-    d2h = 0
     for _ in range(args.steps):
         e2e_ctx.run_cycles(1, SWEEPS_PER_STEP)
         for k in range(len(ds)):
-            p, _e = e2e_ctx.get_dos(k, per_window=True)
-            d2h += p.nbytes
+            e2e_ctx.get_dos(k, per_window=True)
     torch.cuda.synchronize()
     e2e_t = time.perf_counter() - t0
+    h2d, d2h = e2e_ctx.transfer_bytes()          # every copy the library made, counted by it
     e2e_ctx.close()
-    h2d = len(ds) * 88
     e2e = {"value": attempts_per_step * args.steps / e2e_t * world, "unit": "attempts/s",
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-           "includes": "create (descriptors H2D, init kernel) + K steps + per-step ln g read-back"}
+           "includes": "create (descriptors H2D, init kernel) + K steps + per-step ln g read-back; bytes are the "
+                       "library's own count of its host<->device copies (rewl_transfer_bytes)"}
 
     instr = INSTR_PER_TRIAL[0]
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -370,7 +376,30 @@ def _converge(ctx, exchange_interval, poll_cycles, cap_s, tag):
             return done
 
 
-def warm_start_workload(seeds=4, exchange_interval=1000, poll_cycles=5, cap_s=900.0):
+def _stage_table(stage_sweeps):
+    """Per WL stage k (ln f = 2^-k): sweeps the stage took, mean over the
+    windows of all instances, and the sweep at which its last window ended it
+    (mean over instances); from rewl_get_stage_sweeps."""
+    import numpy as np
+    rows = []
+    for k in range(33):
+        durs, ends = [], []
+        for ss in stage_sweeps:
+            end = ss[:, k]
+            if np.all(end < 0):
+                continue
+            prev = ss[:, k - 1] if k > 0 else np.zeros_like(end)
+            prev = np.where(prev < 0, 0, prev)           # a warm start begins later
+            ok = end >= 0
+            durs.extend((end - prev)[ok].tolist())
+            ends.append(int(end[ok].max()))
+        if durs:
+            rows.append({"stage": k, "mean_window_sweeps": float(np.mean(durs)),
+                         "max_window_sweeps": int(np.max(durs)), "last_window_end": float(np.mean(ends))})
+    return rows
+
+
+def warm_start_workload(seeds=4, exchange_interval=1000, poll_cycles=5, cap_s=900.0, models=(0, 1)):
     """Time to ln f = 2^-20, learned warm start vs plain REWL, on one GPU: the
     network is trained on plain-REWL DOS at L = 8..48 (Ising and q=10 Potts),
     then Ising L = 128 and q=10 Potts L = 64 (64 windows x 4 walkers, `seeds`
@@ -389,6 +418,8 @@ def warm_start_workload(seeds=4, exchange_interval=1000, poll_cycles=5, cap_s=90
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
+    clk = ClockSampler(0)
+    clk.__enter__()
     t0 = time.perf_counter()
     train = W.config4_training()
     gen = R.Rewl([R.instance(**d) for d in train], stream=stream)
@@ -408,6 +439,8 @@ def warm_start_workload(seeds=4, exchange_interval=1000, poll_cycles=5, cap_s=90
            "results": []}
     for tgt in W.config4_targets():
         L, model = tgt["L"], tgt["model"]
+        if model not in models:
+            continue
         ds = [dict(tgt, seed=tgt["seed"] + k) for k in range(seeds)]
         runs = {}
         for mode in ("plain", "learned"):
@@ -423,14 +456,15 @@ def warm_start_workload(seeds=4, exchange_interval=1000, poll_cycles=5, cap_s=90
             secs = time.perf_counter() - ts
             sweeps = [int(ctx.counters(k)["conv_sweep"].max()) for k in range(seeds)]
             dos = [ctx.get_dos(k)[0] for k in range(seeds)]
-            runs[mode] = dict(seconds=secs, converged=bool(conv), sweeps_slowest_window=sweeps, dos=dos)
+            runs[mode] = dict(seconds=secs, converged=bool(conv), sweeps_slowest_window=sweeps, dos=dos,
+                              stages=_stage_table([ctx.stage_sweeps(k) for k in range(seeds)]))
             ctx.close()
         res = {"instance": ("Ising" if model == R.ISING else "Potts q=10") + f" L={L}, 64 windows x 4 walkers",
                "seeds": seeds}
         for mode, r in runs.items():
             ent = {"seconds": r["seconds"], "converged": r["converged"],
                    "sweeps_slowest_window": r["sweeps_slowest_window"],
-                   "mean_sweeps": float(np.mean(r["sweeps_slowest_window"]))}
+                   "mean_sweeps": float(np.mean(r["sweeps_slowest_window"])), "per_stage": r["stages"]}
             if model == R.ISING:
                 ex = _golden_ising(L)
                 ent["eps_vs_exact"] = [_mean_rel_err(lg, ex) for lg in r["dos"]]
@@ -446,6 +480,8 @@ def warm_start_workload(seeds=4, exchange_interval=1000, poll_cycles=5, cap_s=90
         res["time_ratio_learned_over_plain"] = res["learned"]["seconds"] / res["plain"]["seconds"]
         out["results"].append(res)
     net.close()
+    clk.__exit__(None, None, None)
+    out["clocks"] = clk.summary()
     print(json.dumps(out))
 
 
@@ -502,6 +538,144 @@ def potts_tc_workload(exchange_interval=1000, poll_cycles=5, cap_s=1500.0):
            "Tc_inf_fit_L_ge_32": tc_inf3, "Tc_inf_fit_L_ge_32_err": tc_err3, "Tc_exact": tc_exact}
     ctx.close()
     print(json.dumps(out))
+
+
+def potts_tc_large_workload(sizes=(32, 48, 64, 80, 100, 128), seeds=4, width=490, stage_final=20,
+                            exchange_interval=1000, poll_cycles=5, cap_s=2400.0, seed0=60000, save=None):
+    """q = 10 Potts transition temperature from C_v maxima (Sec. IV A): every
+    size and seed in one batch, windows of about `width` bins at 75 %
+    overlap, one walker each, run to ln f = 2^-stage_final (lattices above
+    L = 128 stay in global memory during sweeps).  Per size the C_v peak of
+    the mean DOS with the paper's bootstrap error (Sec. II B: per-window
+    pieces of the seeds resampled with replacement, 200 times, each resample
+    joined), and the fit Tc(L) = Tc + a / L^2 against the exact
+    1 / ln(1 + sqrt q).  `save`: write every instance's pieces and geometry to
+    this .npz file (for pooling runs)."""
+    import math
+    import numpy as np
+    import torch
+    from paper_1407_5140_gb300 import rewl as R
+    from paper_1407_5140_gb300 import thermo as TH
+    from paper_1407_5140_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ds = W.potts_fss(sizes=sizes, seeds=seeds, walkers=1, seed0=seed0, width=width)
+    for d in ds:
+        d["ln_f_final"] = 2.0 ** -stage_final
+    with ClockSampler(0) as clk:
+        t_c = time.perf_counter()
+        ctx = R.Rewl([R.instance(**d) for d in ds], stream=stream)
+        ctx.run(1)
+        torch.cuda.synchronize()
+        t_create = time.perf_counter() - t_c
+        t0 = time.perf_counter()
+        conv = _converge(ctx, exchange_interval, poll_cycles, cap_s, "potts fss")
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+    q = ds[0]["q"]
+    tc_exact = 1.0 / math.log(1.0 + math.sqrt(q))
+    per, saved = [], {}
+    for L in sizes:
+        ks = [k for k, d in enumerate(ds) if d["L"] == L]
+        g = ctx.geometry(ks[0])
+        pieces = np.stack([ctx.get_dos(k, per_window=True)[0] for k in ks])
+        _, e = ctx.get_dos(ks[0])
+        saved.update({f"L{L}_pieces": pieces, f"L{L}_lo": g["lo"], f"L{L}_ww": g["ww"], f"L{L}_reach": g["reach"],
+                      f"L{L}_e": e, f"L{L}_conv_sweep": np.array([ctx.counters(k)["conv_sweep"] for k in ks])})
+        ent = {"L": L, "windows": g["h"], "seeds": len(ks),
+               "sweeps_slowest_window": [int(ctx.counters(k)["conv_sweep"].max()) for k in ks],
+               "windows_converged": [int(np.sum(ctx.status(k)["ln_f"] == 0)) for k in ks]}
+        if conv:
+            lo_t, hi_t = 0.66, 0.76
+
+            def tpk(lg, e=e):
+                return TH.cv_peak(lg, e, lo_t, hi_t)[0]
+
+            def cmax(lg, e=e, L=L):
+                return TH.cv_peak(lg, e, lo_t, hi_t)[1] / (L * L)
+
+            _, _, obs = TH.bootstrap_dos(pieces, g["lo"], g["ww"], g["reach"], 1.0, math.log(q), n_resamples=200,
+                                         seed=L, observables={"T_peak": tpk, "C_max_per_site": cmax})
+            ent.update({"T_peak": obs["T_peak"][0], "T_peak_bootstrap_err": obs["T_peak"][1],
+                        "C_max_per_site": obs["C_max_per_site"][0], "C_max_bootstrap_err": obs["C_max_per_site"][1],
+                        "log_sum_minus_N_ln_q": [_log_sum(ctx.get_dos(k)[0]) - L * L * math.log(q) for k in ks]})
+        per.append(ent)
+    ctx.close()
+    if save:
+        np.savez_compressed(save, **saved)
+    fits = {}
+    if conv and seeds > 1:
+        Ls = [p["L"] for p in per]
+        tcs = [p["T_peak"] for p in per]
+        errs = [max(p["T_peak_bootstrap_err"], 1e-7) for p in per]
+        for lmin in sorted({min(Ls), 64, 100} & set(range(min(Ls), max(Ls)))):
+            idx = [i for i, L in enumerate(Ls) if L >= lmin]
+            if len(idx) >= 3:
+                t, e_, a = TH.extrapolate_tc([Ls[i] for i in idx], [tcs[i] for i in idx], [errs[i] for i in idx])
+                fits[f"L_ge_{lmin}"] = {"Tc_inf": t, "err": e_, "a": a}
+    out = {"metric": "q=10 Potts transition temperature from C_v maxima", "n_gpus": 1, "data": "synthetic",
+           "workload": f"q=10 Potts L={list(sizes)}, windows of ~{width} bins at 75 %, 1 walker each, {seeds} seeds "
+                       f"per size in one batch, exchange every {exchange_interval} sweeps, "
+                       f"ln f_final = 2^-{stage_final}",
+           "converged": bool(conv), "seconds": secs, "create_and_first_sweep_s": t_create,
+           "walkers": int(sum(d["n_windows"] for d in ds)), "sizes": per, "fits": fits, "Tc_exact": tc_exact,
+           "clocks": clk.summary()}
+    print(json.dumps(out))
+
+
+def config_throughput_workload(steps=3, warmup=3, sweeps=10000):
+    """Attempts/s of the other batch shapes on one GPU: the single 2D Ising
+    L = 8 instance (4 windows x 1 walker), the q = 10 Potts L = 32 instance
+    (32 windows x 8 walkers) and the uneven batch (64 Ising instances, L from
+    {16..64}, and 32 q = 10 Potts instances, L from {16, 24, 32}).  One step =
+    `sweeps` sweeps + one exchange, CUDA events on the library's stream, L2
+    flushed between steps; the issue-rate fraction counts 110 (Ising) and 146
+    (Potts) algorithmic thread instructions per trial against the sweep
+    launches' time."""
+    import torch
+    from paper_1407_5140_gb300 import rewl as R
+    from paper_1407_5140_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = n_sm * 4 * 32 * MAX_SM_MHZ * 1e6
+    rows = {}
+    with ClockSampler(0) as clk:
+        for name, ds in (("ising_L8_4x1", W.config0()), ("potts_q10_L32_32x8", W.config2()),
+                         ("uneven_64_ising_32_potts", W.config3())):
+            ctx = R.Rewl([R.instance(**d) for d in ds], stream=stream)
+            for _ in range(warmup):
+                ctx.run(sweeps)
+                ctx.exchange()
+            torch.cuda.synchronize()
+            tot, ks = [], []
+            for _ in range(steps):
+                flush.fill_(1)
+                a, m, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                a.record(stream)
+                ctx.run(sweeps)
+                m.record(stream)
+                ctx.exchange()
+                b.record(stream)
+                b.synchronize()
+                tot.append(a.elapsed_time(b) / 1e3)
+                ks.append(a.elapsed_time(m) / 1e3)
+            ctx.close()
+            att = W.attempts_per_sweep(ds) * sweeps
+            instr = sum(INSTR_PER_TRIAL[d["model"]] * d["n_windows"] * d["walkers_per_window"] * d["L"] ** 2
+                        for d in ds) * sweeps
+            t, k = sum(tot) / steps, sum(ks) / steps
+            rows[name] = {"instances": len(ds), "walkers": sum(d["n_windows"] * d["walkers_per_window"] for d in ds),
+                          "attempts_per_s": att / t, "ms_per_step": t * 1e3,
+                          "issue_rate_frac": instr / k / peak, "sweeps_per_step": sweeps}
+    print(json.dumps({"metric": "WL flip attempts/s per batch shape", "unit": "attempts/s", "n_gpus": 1,
+                      "data": "synthetic", "steps": steps, "warmup": warmup, "l2": "flushed between steps",
+                      "results": rows, "clocks": clk.summary()}))
 
 
 def exchange_study_workload(intervals=(100, 1000, 10000, 0), cap_s=600.0):
@@ -642,6 +816,8 @@ def balanced_converge_workload(seeds=4, L=64, q=10, h=64, m=4, overlap=0.75, exc
         ctx.close()
         return conv, dos, secs, ok
 
+    clk = ClockSampler(0)
+    clk.__enter__()
     pconv, _, psecs, pok = run(40000, (elo, ehi), 1.0)
     t_win = np.mean(np.array(pconv, float), axis=0)
     blo, bhi = WN.balanced_windows(elo, ehi, t_win, B, overlap, min_w)
@@ -661,11 +837,93 @@ def balanced_converge_workload(seeds=4, L=64, q=10, h=64, m=4, overlap=0.75, exc
                                               for lg in dos]}
         if model == W.ISING:
             out[name]["eps_vs_exact"] = [_mean_rel_err(lg, _golden_ising(L)) for lg in dos]
+    clk.__exit__(None, None, None)
+    out["clocks"] = clk.summary()
     if compare_equal:
         out["eps_balanced_vs_equal"] = [_mean_rel_err(a, b) for a, b in zip(res["balanced"], res["equal"])]
         out["eps_equal_seed_to_seed"] = [_mean_rel_err(res["equal"][k], res["equal"][0]) for k in range(1, seeds)]
         out["sweep_ratio_balanced_over_equal"] = out["balanced"]["mean_sweeps"] / out["equal"]["mean_sweeps"]
         out["time_ratio_balanced_over_equal"] = out["balanced"]["seconds"] / out["equal"]["seconds"]
+    print(json.dumps(out))
+
+
+def self_tuning_workload(L=128, h=64, m=4, seeds=4, overlap=0.75, exchange_interval=1000, model=0, q=2,
+                         tune_at=(0, 1, 2, 3, 4, 5), tune_avg=1, skip_equal=False):
+    """Time to ln f = 2^-20 on equal and on self-tuning windows (Sec. V), the
+    same seeds on both: the self-tuning batch starts on equal windows; after
+    each stage in `tune_at` it resizes the windows from the sweeps per window
+    of the last `tune_avg` stages (when the slowest took more than 1.2 times
+    the mean) and continues from each instance's joined ln g at the next
+    ln f.  Ising L = 128, 64 windows x 4 walkers, `seeds` instances per
+    batch; error against the exact DOS; per-window sweeps of every stage."""
+    import numpy as np
+    import torch
+    from paper_1407_5140_gb300 import rewl as R
+    from paper_1407_5140_gb300 import windows as WN
+    from paper_1407_5140_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    B = L * L + 1 if model == W.ISING else 2 * L * L + 1
+    min_w = 5 if model == W.ISING else 9
+    elo, ehi = WN.equal_windows(B, h, overlap)
+    exact = _golden_ising(L) if model == W.ISING else None
+    name_m = "Ising" if model == W.ISING else f"q={q} Potts"
+    out = {"metric": "time to ln f=2^-20, equal vs self-tuning windows", "unit": "s", "n_gpus": 1,
+           "data": "synthetic", "workload": f"{name_m} L={L}, {h} windows x {m} walkers, {seeds} seeds in one "
+                                             f"batch, exchange every {exchange_interval} sweeps",
+           "tune_at": list(tune_at), "tune_avg": tune_avg}
+
+    def make(lo, hi):
+        ds = [W._inst(model, L, q, h, m, 50000 + s) for s in range(seeds)]
+        return R.Rewl([R.instance(**d) for d in ds], stream=stream, windows=[(lo, hi)] * seeds)
+
+    def errs(ctx):
+        if exact is None:
+            return None
+        return [_mean_rel_err(ctx.get_dos(i)[0], exact) for i in range(seeds)]
+
+    def per_window(ctx):
+        # mean over the instances of each window's sweeps in each stage run here
+        ss = [ctx.stage_sweeps(i) for i in range(seeds)]
+        rows = {}
+        for k in range(33):
+            d = [WN.stage_durations(s, k) for s in ss]
+            if all(x is not None for x in d) and np.all(np.array([s[:, k] for s in ss]) >= 0):
+                rows[k] = np.mean(d, axis=0).round(1).tolist()
+        return rows
+
+    with ClockSampler(0) as clk:
+        if not skip_equal:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx = make(elo, ehi)
+            while not ctx.run_to_convergence(exchange_interval, 50 * exchange_interval, poll_cycles=5):
+                pass
+            torch.cuda.synchronize()
+            out["equal"] = {"seconds": time.perf_counter() - t0,
+                            "sweeps_slowest_window": [int(ctx.counters(i)["conv_sweep"].max()) for i in range(seeds)],
+                            "eps_vs_exact": errs(ctx),
+                            "stage_table": _stage_table([ctx.stage_sweeps(i) for i in range(seeds)]),
+                            "per_window_stage_sweeps": per_window(ctx)}
+            ctx.close()
+            print(f"[self-tuning] equal windows: {out['equal']['seconds']:.1f} s", file=sys.stderr, flush=True)
+        t0 = time.perf_counter()
+        ctx, (flo, fhi), resizes, sweeps = WN.self_tuning_run(
+            make, (elo, ehi), B, overlap, min_w, exchange_interval, n_inst=seeds, tune_at=tune_at, tune_avg=tune_avg,
+            max_width=3 * int(ehi[0] - elo[0] + 1),
+            log=lambda msg: print(f"[self-tuning] {msg}", file=sys.stderr, flush=True))
+        torch.cuda.synchronize()
+        out["self_tuning"] = {"seconds": time.perf_counter() - t0, "sweeps_run": sweeps, "resizes": resizes,
+                              "eps_vs_exact": errs(ctx),
+                              "final_widths": (np.asarray(fhi) - np.asarray(flo) + 1).tolist(),
+                              "stage_table_last_batch": _stage_table([ctx.stage_sweeps(i) for i in range(seeds)]),
+                              "per_window_stage_sweeps_last_batch": per_window(ctx)}
+        ctx.close()
+    out["clocks"] = clk.summary()
+    if not skip_equal:
+        out["time_ratio_self_tuning_over_equal"] = out["self_tuning"]["seconds"] / out["equal"]["seconds"]
     print(json.dumps(out))
 
 
@@ -680,8 +938,21 @@ def main():
                     help="skip the time-to-converge runs (Config 0 and Config 2 to ln f = 2^-20)")
     ap.add_argument("--profile-case", action="store_true",
                     help="only the workload's launch shape with 20 sweeps per launch (for ncu captures)")
+    ap.add_argument("--sizes", default=None, help="potts-tc-large: comma-separated lattice sides")
+    ap.add_argument("--seeds", type=int, default=None, help="potts-tc-large: independent runs per size")
+    ap.add_argument("--width", type=int, default=None, help="potts-tc-large: bins per window")
+    ap.add_argument("--stage-final", type=int, default=None, help="potts-tc-large: last WL stage (ln f = 2^-k)")
+    ap.add_argument("--cap-s", type=float, default=None, help="potts-tc-large: wall-time cap of the run")
+    ap.add_argument("--seed0", type=int, default=None, help="potts-tc-large: first seed")
+    ap.add_argument("--save", default=None, help="potts-tc-large: .npz file for the per-window pieces")
+    ap.add_argument("--ising-only", action="store_true", help="warm-start: the Ising L=128 target only")
+    ap.add_argument("--tune-at", default=None,
+                    help="self-tuning: comma-separated stages after which windows may be resized")
+    ap.add_argument("--tune-avg", type=int, default=1,
+                    help="self-tuning: stages averaged for each resize decision")
+    ap.add_argument("--skip-equal", action="store_true", help="self-tuning: run the self-tuning batch only")
     ap.add_argument("--workload", default="throughput", choices=["throughput", "warm-start", "potts-tc", "exchange", "balanced-windows",
-                             "balanced-converge", "balanced-converge-ising"],
+                             "balanced-converge", "balanced-converge-ising", "self-tuning", "potts-tc-large", "configs"],
                     help="warm-start: time to converge, learned vs plain (Ising L=128, Potts q=10 L=64); "
                          "potts-tc: q=10 Potts transition from C_v maxima, L=16..64; "
                          "exchange: sweeps to finish WL iterations vs exchange frequency; "
@@ -692,7 +963,7 @@ def main():
         profile_case()
         return
     if args.workload == "warm-start":
-        warm_start_workload()
+        warm_start_workload(models=(0,) if args.ising_only else (0, 1))
         return
     if args.workload == "potts-tc":
         potts_tc_workload()
@@ -708,6 +979,29 @@ def main():
         return
     if args.workload == "balanced-converge-ising":      # Ising L=128, balanced windows only
         balanced_converge_workload(L=128, q=2, model=0, compare_equal=False)
+        return
+    if args.workload == "self-tuning":
+        self_tuning_workload(tune_at=tuple(int(x) for x in args.tune_at.split(",")) if args.tune_at else (0, 1, 2, 3, 4, 5),
+                             tune_avg=args.tune_avg, skip_equal=args.skip_equal)
+        return
+    if args.workload == "potts-tc-large":
+        kw = {}
+        if args.sizes:
+            kw["sizes"] = tuple(int(x) for x in args.sizes.split(","))
+        if args.seeds:
+            kw["seeds"] = args.seeds
+        if args.width:
+            kw["width"] = args.width
+        if args.stage_final:
+            kw["stage_final"] = args.stage_final
+        if args.cap_s:
+            kw["cap_s"] = args.cap_s
+        if args.seed0 is not None:
+            kw["seed0"] = args.seed0
+        potts_tc_large_workload(save=args.save, **kw)
+        return
+    if args.workload == "configs":
+        config_throughput_workload()
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

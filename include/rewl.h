@@ -61,7 +61,7 @@ typedef enum { REWL_ISING = 0, REWL_POTTS = 1 } rewl_model;
  * window, overlap o with the next-lower window). */
 typedef struct rewl_instance {
     int32_t model;              /* rewl_model                                   */
-    int32_t L;                  /* even, 4 <= L <= 128                          */
+    int32_t L;                  /* even, 4 <= L <= 512                          */
     int32_t q;                  /* Potts states, 2..127 (ignored for Ising)     */
     int32_t n_windows;          /* h >= 1                                       */
     int64_t e_min, e_max;       /* inclusive energy range, on the bin grid      */
@@ -155,6 +155,13 @@ rewl_status rewl_join_pieces(int h, int w, int B, const int32_t *lo, const int32
                              const uint8_t *reach, double bin_width, double ln_g_first,
                              const double *pieces, double *ln_g);
 
+/* Sweep count at which each window of instance `inst` ended each Wang-Landau
+ * stage k = 0..32 (ln f = 2^-k) with the merge of its walkers' ln g (Sec. II A):
+ * stage_sweep[i * 33 + k] for window i, -1 for stages not (yet) ended there
+ * (h * 33 values).  The sweeps a stage took are the differences between
+ * consecutive entries. */
+rewl_status rewl_get_stage_sweeps(rewl_ctx *ctx, int inst, int64_t *stage_sweep);
+
 /* Progress: all_converged over all instances; sweeps done; ln f per window of
  * instance `inst` (h values, 0 once converged; may be NULL). */
 rewl_status rewl_status_query(rewl_ctx *ctx, int inst, int *all_converged, double *ln_f_per_window,
@@ -201,15 +208,28 @@ rewl_status rewl_get_counters(rewl_ctx *ctx, int inst, uint64_t *ex_prop, uint64
  * REWL_OPT_MAX_SWEEPS_PER_LAUNCH: split long rewl_run calls (>= 1).
  * REWL_OPT_AUTOTUNE: 1 (default) = before the first run, time a few launch
  * shapes on a shadow copy of the batch (same descriptors, its own memory) and
- * keep the fastest; 0 = shape rule only.  Shapes never change results.
+ * keep the fastest; 0 = shape rule only.
+ * REWL_OPT_LATTICE_PLACEMENT: where the sweep kernel keeps the walkers'
+ * lattices while it runs: 0 (default) = shared memory up to 16 KB per walker
+ * (Potts L <= 128, Ising L <= 352), global memory above (e.g. the paper's
+ * Potts L = 200...400); 1 = always global; 2 = always shared (contexts
+ * whose windows' state then exceeds shared memory fail to plan, REWL_EINVAL).
+ * Shapes and placement never change results.
  * Launch-shape options may only be set before the first run. */
 enum { REWL_OPT_CHECK_EVERY = 1, REWL_OPT_PRODUCER_WARPS = 2, REWL_OPT_WINDOWS_PER_CTA = 3,
-       REWL_OPT_MAX_SWEEPS_PER_LAUNCH = 4, REWL_OPT_AUTOTUNE = 5 };
+       REWL_OPT_MAX_SWEEPS_PER_LAUNCH = 4, REWL_OPT_AUTOTUNE = 5, REWL_OPT_LATTICE_PLACEMENT = 6 };
 rewl_status rewl_set_option(rewl_ctx *ctx, int option, long value);
 
 /* Number of kernel launches this context enqueued so far (graph replays count
  * each node). */
 long rewl_launch_count(const rewl_ctx *ctx);
+
+/* Bytes this context copied host -> device (*h2d) and device -> host (*d2h)
+ * since it was created: descriptors and windows at creation, warm-start ln g,
+ * checkpoint loads; every read-out, progress poll and error-word check.
+ * Copies the caller makes itself are not included.  Either pointer may be
+ * NULL; REWL_EINVAL for a NULL context. */
+rewl_status rewl_transfer_bytes(const rewl_ctx *ctx, int64_t *h2d, int64_t *d2h);
 
 /* Checkpoint: the complete state (lattices, energies, ln g, H, stages,
  * latches, Philox counters, exchange counter) to a file; loading it resumes

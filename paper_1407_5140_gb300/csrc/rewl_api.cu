@@ -50,6 +50,7 @@ struct rewl_ctx {
     uint8_t *d_conv = nullptr;
     int64_t *d_conv_sweep = nullptr;
     ull *d_ex_prop = nullptr, *d_ex_acc = nullptr;
+    int64_t *d_stage_sweep = nullptr;
     int32_t *d_cfg = nullptr, *d_E = nullptr, *d_bin = nullptr, *d_replica = nullptr, *d_slot_inst = nullptr;
     ull *d_draw = nullptr, *d_nacc = nullptr;
     uint8_t *d_latch = nullptr;
@@ -68,6 +69,7 @@ struct rewl_ctx {
     long check_every = 1;
     long max_sweeps_per_launch = 1L << 30;
     int force_producers = 0, force_wpc = 0;
+    int lattice_mode = 0;               // 0: by size, 1: global memory, 2: shared memory
     int tune_mode = 1;                  // 1: measure candidate shapes, 0: rule only
     int tune_target = 0, tune_bias = 0; // chosen walkers-per-block target / producer bias
     bool planned = false;
@@ -75,11 +77,19 @@ struct rewl_ctx {
     long graph_sweeps = -1;
     long graph_launches = 0;
     long launches = 0;
+    long long bytes_h2d = 0, bytes_d2h = 0;   // host<->device bytes the library copied
     int failed = 0;
     std::string err;
 };
 
 static thread_local std::string g_create_error;
+
+// Largest lattice side (the site -> (row, column) division by a multiply-high
+// with ceil(2^32 / L) is exact for every site of an L x L lattice while
+// L^3 < 2^32); lattices above kSharedLatticeBytes per walker stay in global
+// memory during sweeps (Potts L > 128, Ising L > 352).
+static const int kMaxL = 512;
+static const long long kSharedLatticeBytes = 16384;
 
 static rewl_status fail(rewl_ctx *c, rewl_status s, const std::string &msg)
 {
@@ -90,6 +100,26 @@ static rewl_status fail(rewl_ctx *c, rewl_status s, const std::string &msg)
         g_create_error = msg;
     }
     return s;
+}
+
+// Every host<->device copy of a context goes through these, which count its
+// bytes (rewl_transfer_bytes).
+static cudaError_t h2d(rewl_ctx *ctx, void *dst, const void *src, size_t n, cudaStream_t s)
+{
+    ctx->bytes_h2d += (long long)n;
+    return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s);
+}
+
+static cudaError_t h2d_sync(rewl_ctx *ctx, void *dst, const void *src, size_t n)
+{
+    ctx->bytes_h2d += (long long)n;
+    return cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice);
+}
+
+static cudaError_t d2h(rewl_ctx *ctx, void *dst, const void *src, size_t n)
+{
+    ctx->bytes_d2h += (long long)n;
+    return cudaMemcpy(dst, src, n, cudaMemcpyDeviceToHost);
 }
 
 #define CK(call)                                                                               \
@@ -120,7 +150,7 @@ static rewl_status build_instance(const rewl_instance &d, HostInst &hi, std::str
 {
     char buf[256];
     if (d.model != REWL_ISING && d.model != REWL_POTTS) { why = "model must be REWL_ISING or REWL_POTTS"; return REWL_EINVAL; }
-    if (d.L < 4 || d.L > 128 || d.L % 2) { why = "L must be even, 4 <= L <= 128"; return REWL_EINVAL; }
+    if (d.L < 4 || d.L > kMaxL || d.L % 2) { why = "L must be even, 4 <= L <= 512"; return REWL_EINVAL; }
     const int q = d.model == REWL_ISING ? 2 : d.q;
     if (d.model == REWL_POTTS && (q < 2 || q > 127)) { why = "q must be in 2..127"; return REWL_EINVAL; }
     if (d.n_windows < 1 || d.n_windows > 65535) { why = "n_windows must be in 1..65535"; return REWL_EINVAL; }
@@ -305,6 +335,7 @@ static rewl_status create_batch(rewl_ctx **out, const rewl_instance *inst, int n
     CK(dalloc(&ctx->d_conv_sweep, win));
     CK(dalloc(&ctx->d_ex_prop, win));
     CK(dalloc(&ctx->d_ex_acc, win));
+    CK(dalloc(&ctx->d_stage_sweep, (size_t)win * kMaxStages));
     CK(dalloc(&ctx->d_cfg, slot));
     CK(dalloc(&ctx->d_E, slot));
     CK(dalloc(&ctx->d_bin, slot));
@@ -323,19 +354,20 @@ static rewl_status create_batch(rewl_ctx **out, const rewl_instance *inst, int n
     CK(dalloc(&ctx->d_ex0, ex0.size()));
     CK(dalloc(&ctx->d_ex1, ex1.size()));
     cudaStream_t s = ctx->stream;
-    CK(cudaMemcpyAsync(ctx->d_inst, idev.data(), sizeof(InstDev) * n_inst, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ctx->d_lo, lo_all.data(), 4 * win, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ctx->d_ww, ww_all.data(), 4 * win, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ctx->d_nreach, nreach_all.data(), 4 * win, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ctx->d_reach, reach_all.data(), rch, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ctx->d_slot_inst, slot_inst.data(), 4 * slot, cudaMemcpyHostToDevice, s));
-    if (!ex0.empty()) CK(cudaMemcpyAsync(ctx->d_ex0, ex0.data(), sizeof(ExTask) * ex0.size(), cudaMemcpyHostToDevice, s));
-    if (!ex1.empty()) CK(cudaMemcpyAsync(ctx->d_ex1, ex1.data(), sizeof(ExTask) * ex1.size(), cudaMemcpyHostToDevice, s));
+    CK(h2d(ctx, ctx->d_inst, idev.data(), sizeof(InstDev) * n_inst, s));
+    CK(h2d(ctx, ctx->d_lo, lo_all.data(), 4 * win, s));
+    CK(h2d(ctx, ctx->d_ww, ww_all.data(), 4 * win, s));
+    CK(h2d(ctx, ctx->d_nreach, nreach_all.data(), 4 * win, s));
+    CK(h2d(ctx, ctx->d_reach, reach_all.data(), rch, s));
+    CK(h2d(ctx, ctx->d_slot_inst, slot_inst.data(), 4 * slot, s));
+    if (!ex0.empty()) CK(h2d(ctx, ctx->d_ex0, ex0.data(), sizeof(ExTask) * ex0.size(), s));
+    if (!ex1.empty()) CK(h2d(ctx, ctx->d_ex1, ex1.data(), sizeof(ExTask) * ex1.size(), s));
     CK(cudaMemsetAsync(ctx->d_stage, 0, 4 * win, s));
     CK(cudaMemsetAsync(ctx->d_conv, 0, win, s));
     CK(cudaMemsetAsync(ctx->d_conv_sweep, 0xFF, 8 * win, s));
     CK(cudaMemsetAsync(ctx->d_ex_prop, 0, 8 * win, s));
     CK(cudaMemsetAsync(ctx->d_ex_acc, 0, 8 * win, s));
+    CK(cudaMemsetAsync(ctx->d_stage_sweep, 0xFF, 8 * (size_t)win * kMaxStages, s));
     CK(cudaMemsetAsync(ctx->d_lng, 0, 8 * lng, s));
     CK(cudaMemsetAsync(ctx->d_lng0, 0, 8 * lng, s));
     CK(cudaMemsetAsync(ctx->d_H, 0, 4 * lng, s));
@@ -351,6 +383,7 @@ static rewl_status create_batch(rewl_ctx **out, const rewl_instance *inst, int n
     st.conv_sweep = ctx->d_conv_sweep;
     st.ex_prop = ctx->d_ex_prop;
     st.ex_acc = ctx->d_ex_acc;
+    st.stage_sweep = reinterpret_cast<long long *>(ctx->d_stage_sweep);
     st.cfg = ctx->d_cfg;
     st.E = ctx->d_E;
     st.bin = ctx->d_bin;
@@ -371,7 +404,7 @@ static rewl_status create_batch(rewl_ctx **out, const rewl_instance *inst, int n
     if (e) return fail(ctx, REWL_ECUDA, std::string("init launch: ") + cudaGetErrorString((cudaError_t)e));
     CK(cudaStreamSynchronize(s));
     int herr = 0;
-    CK(cudaMemcpy(&herr, ctx->d_error, 4, cudaMemcpyDeviceToHost));
+    CK(d2h(ctx, &herr, ctx->d_error, 4));
     if (herr) return fail(ctx, REWL_EDEVICE, "init: a walker did not reach its window");
     return REWL_OK;
 }
@@ -408,7 +441,7 @@ extern "C" void rewl_destroy(rewl_ctx *ctx)
         if (c.done) cudaEventDestroy(c.done);
     }
     void *bufs[] = {ctx->d_inst, ctx->d_lo, ctx->d_ww, ctx->d_nreach, ctx->d_stage, ctx->d_conv, ctx->d_conv_sweep,
-                    ctx->d_ex_prop, ctx->d_ex_acc, ctx->d_cfg, ctx->d_E, ctx->d_bin, ctx->d_replica,
+                    ctx->d_ex_prop, ctx->d_ex_acc, ctx->d_stage_sweep, ctx->d_cfg, ctx->d_E, ctx->d_bin, ctx->d_replica,
                     ctx->d_slot_inst, ctx->d_draw, ctx->d_nacc, ctx->d_latch, ctx->d_lng, ctx->d_lng0, ctx->d_H,
                     ctx->d_lat, ctx->d_reach, ctx->d_counters, ctx->d_error, ctx->d_ex0, ctx->d_ex1};
     for (void *b : bufs)
@@ -429,7 +462,13 @@ void rewl::plan_class(rewl_ctx *ctx, int ci, int wpc, int producers)
     c.items.clear();
     for (int k : c.insts) {
         const InstDev &I = ctx->inst[k].dev;
-        for (int w0 = 0; w0 < I.h; w0 += wpc) c.items.push_back(WorkItem{k, w0, std::min(wpc, I.h - w0), 0});
+        const HostInst &hi = ctx->inst[k];
+        for (int w0 = 0; w0 < I.h; w0 += wpc) {
+            const int n = std::min(wpc, I.h - w0);
+            int wrow = 0;
+            for (int i = w0; i < w0 + n; ++i) wrow = std::max(wrow, hi.ww[i]);
+            c.items.push_back(WorkItem{k, w0, n, wrow});
+        }
     }
     const int nw = wpc * c.m;
     c.sl.n_items = (int)c.items.size();
@@ -491,6 +530,7 @@ static void measure_shapes(rewl_ctx *ctx)
             sh->tune_mode = 0;
             sh->tune_target = t;
             sh->tune_bias = b;
+            sh->lattice_mode = ctx->lattice_mode;
             sh->check_every = ctx->check_every;
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             float ms = -1.f;
@@ -511,6 +551,37 @@ static void measure_shapes(rewl_ctx *ctx)
     cudaGetLastError();
 }
 
+// Blocks whose windows are narrower than the instance's widest need shorter
+// ln g rows in shared memory: split each size class into launches by the
+// block row width (rounded up to 64 bins), each asking only for the shared
+// memory its widest block needs.  Equal-width windows stay one launch.
+static void split_by_row(rewl_ctx *ctx)
+{
+    std::vector<SizeClass> out;
+    for (auto &c : ctx->classes) {
+        std::map<int, std::vector<WorkItem>> by;
+        for (const WorkItem &it : c.items) by[std::min(c.w, (it.wrow + 63) / 64 * 64)].push_back(it);
+        if (by.size() <= 1) {
+            out.push_back(c);
+            continue;
+        }
+        for (auto &kv : by) {
+            SizeClass d = c;
+            d.items = kv.second;
+            int wmax = 0, wpc = 0;
+            for (const WorkItem &it : d.items) {
+                wmax = std::max(wmax, it.wrow);
+                wpc = std::max(wpc, it.n_win);
+            }
+            d.sl.n_items = (int)d.items.size();
+            d.sl.smem = sweep_smem_bytes(wpc * c.m, wpc, wmax, c.lat_words, c.sl.producers, c.N);
+            d.sl.max_w = wmax;
+            out.push_back(d);
+        }
+    }
+    ctx->classes.swap(out);
+}
+
 static rewl_status plan(rewl_ctx *ctx)
 {
     if (ctx->planned) return REWL_OK;
@@ -528,13 +599,19 @@ static rewl_status plan(rewl_ctx *ctx)
             c.w = I.w;
             c.m = I.m;
             c.N = I.N;
-            c.lat_words = I.lat_words;
+            // lattices larger than kSharedLatticeBytes stay in global memory
+            // (lat_words counts the words a walker keeps in shared memory)
+            const bool glat = ctx->lattice_mode == 1 ||
+                              (ctx->lattice_mode == 0 && 4LL * I.lat_words > kSharedLatticeBytes);
+            c.lat_words = glat ? 0 : I.lat_words;
+            c.sl.glat = glat ? 1 : 0;
             ctx->classes.push_back(c);
             f = key2c.emplace(key, (int)ctx->classes.size() - 1).first;
         }
         ctx->classes[f->second].insts.push_back(k);
     }
     if (autotune_plan(ctx)) return fail(ctx, REWL_EINVAL, "no launch configuration fits a window's walkers in shared memory");
+    split_by_row(ctx);
     // launch the classes with the largest blocks first: the block scheduler then
     // packs the smaller blocks into the shared memory the large ones leave free
     std::stable_sort(ctx->classes.begin(), ctx->classes.end(),
@@ -542,19 +619,20 @@ static rewl_status plan(rewl_ctx *ctx)
     for (auto &c : ctx->classes) {
         if (c.sl.smem > 227 * 1024) return fail(ctx, REWL_EINVAL, "window state exceeds shared memory");
         CK(dalloc(&c.d_items, c.items.size()));
-        CK(cudaMemcpy(c.d_items, c.items.data(), sizeof(WorkItem) * c.items.size(), cudaMemcpyHostToDevice));
+        CK(h2d_sync(ctx, c.d_items, c.items.data(), sizeof(WorkItem) * c.items.size()));
         c.sl.items = c.d_items;
         CK(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
     }
-    // one kernel per model serves every class of that model: allow the largest
-    // dynamic shared memory any of them needs
-    for (int model = 0; model < 2; ++model) {
+    // one kernel per model and lattice placement serves every class of that
+    // kind: allow the largest dynamic shared memory any of them needs
+    for (int kind = 0; kind < 4; ++kind) {
+        const int model = kind >> 1, glat = kind & 1;
         int smem = 0;
         for (auto &c : ctx->classes)
-            if (c.model == model) smem = std::max(smem, c.sl.smem);
+            if (c.model == model && c.sl.glat == glat) smem = std::max(smem, c.sl.smem);
         if (!smem) continue;
-        int e = prepare_sweep(model, 0, smem);
+        int e = prepare_sweep(model, glat != 0, smem);
         if (e) return fail(ctx, REWL_ECUDA, std::string("sweep kernel attributes: ") + cudaGetErrorString((cudaError_t)e));
     }
     ctx->planned = true;
@@ -663,7 +741,7 @@ static rewl_status sync_and_check(rewl_ctx *ctx)
 {
     CK(cudaStreamSynchronize(ctx->stream));
     int herr = 0;
-    CK(cudaMemcpy(&herr, ctx->d_error, 4, cudaMemcpyDeviceToHost));
+    CK(d2h(ctx, &herr, ctx->d_error, 4));
     if (herr & kErrRange) return fail(ctx, REWL_EDEVICE, "ln g left the FP64-exact range |ln g| < 2^21");
     if (herr) return fail(ctx, REWL_EDEVICE, "device error word " + std::to_string(herr));
     return REWL_OK;
@@ -681,7 +759,7 @@ extern "C" rewl_status rewl_run_to_convergence(rewl_ctx *ctx, long exchange_inte
     long done = 0;
     for (;;) {
         if ((s = sync_and_check(ctx))) return s;
-        CK(cudaMemcpy(conv.data(), ctx->d_conv, ctx->n_win, cudaMemcpyDeviceToHost));
+        CK(d2h(ctx, conv.data(), ctx->d_conv, ctx->n_win));
         if (std::all_of(conv.begin(), conv.end(), [](uint8_t v) { return v != 0; })) {
             if (converged) *converged = 1;
             return REWL_OK;
@@ -727,11 +805,11 @@ extern "C" rewl_status rewl_window_widths(rewl_ctx *ctx, int inst, int32_t *ww)
 }
 
 template <class T>
-static cudaError_t dget(std::vector<T> &v, const T *d, size_t n)
+static cudaError_t dget(rewl_ctx *ctx, std::vector<T> &v, const T *d, size_t n)
 {
     v.resize(n);
     if (n == 0) return cudaSuccess;
-    return cudaMemcpy(v.data(), d, n * sizeof(T), cudaMemcpyDeviceToHost);
+    return d2h(ctx, v.data(), d, n * sizeof(T));
 }
 
 extern "C" rewl_status rewl_get_state(rewl_ctx *ctx, int inst, int8_t *spins, int64_t *E, int32_t *bin,
@@ -744,10 +822,10 @@ extern "C" rewl_status rewl_get_state(rewl_ctx *ctx, int inst, int8_t *spins, in
     const InstDev &I = ctx->inst[inst].dev;
     const int nw = I.h * I.m;
     std::vector<int32_t> cfg, e, b, rep;
-    CK(dget(cfg, ctx->d_cfg + I.slot0, nw));
+    CK(dget(ctx, cfg, ctx->d_cfg + I.slot0, nw));
     if (spins) {
         std::vector<uint32_t> lat;
-        CK(dget(lat, ctx->d_lat + I.lat_off, (size_t)nw * I.lat_words));
+        CK(dget(ctx, lat, ctx->d_lat + I.lat_off, (size_t)nw * I.lat_words));
         for (int k = 0; k < nw; ++k) {
             const uint32_t *l = lat.data() + (size_t)cfg[k] * I.lat_words;
             for (int y = 0; y < I.L; ++y)
@@ -760,13 +838,13 @@ extern "C" rewl_status rewl_get_state(rewl_ctx *ctx, int inst, int8_t *spins, in
         }
     }
     if (E) {
-        CK(dget(e, ctx->d_E + I.slot0, nw));
+        CK(dget(ctx, e, ctx->d_E + I.slot0, nw));
         for (int k = 0; k < nw; ++k) E[k] = e[k];
     }
-    if (bin) CK(cudaMemcpy(bin, ctx->d_bin + I.slot0, 4 * nw, cudaMemcpyDeviceToHost));
+    if (bin) CK(d2h(ctx, bin, ctx->d_bin + I.slot0, 4 * nw));
     if (ln_g) {
         std::vector<long long> u;
-        CK(dget(u, ctx->d_lng + I.lng_off, (size_t)nw * I.w));
+        CK(dget(ctx, u, ctx->d_lng + I.lng_off, (size_t)nw * I.w));
         for (size_t i = 0; i < u.size(); ++i) ln_g[i] = std::ldexp((double)u[i], -32);
     }
     if (H) {
@@ -775,11 +853,11 @@ extern "C" rewl_status rewl_get_state(rewl_ctx *ctx, int inst, int8_t *spins, in
         std::vector<long long> u, u0;
         std::vector<int32_t> sg;
         std::vector<uint8_t> cv;
-        CK(dget(u, ctx->d_lng + I.lng_off, (size_t)nw * I.w));
-        CK(dget(u0, ctx->d_lng0 + I.lng_off, (size_t)nw * I.w));
-        CK(dget(sg, ctx->d_stage + I.win0, I.h));
-        CK(dget(cv, ctx->d_conv + I.win0, I.h));
-        CK(cudaMemcpy(H, ctx->d_H + I.lng_off, 4 * (size_t)nw * I.w, cudaMemcpyDeviceToHost));
+        CK(dget(ctx, u, ctx->d_lng + I.lng_off, (size_t)nw * I.w));
+        CK(dget(ctx, u0, ctx->d_lng0 + I.lng_off, (size_t)nw * I.w));
+        CK(dget(ctx, sg, ctx->d_stage + I.win0, I.h));
+        CK(dget(ctx, cv, ctx->d_conv + I.win0, I.h));
+        CK(d2h(ctx, H, ctx->d_H + I.lng_off, 4 * (size_t)nw * I.w));
         for (int k = 0; k < nw; ++k) {
             const int win = k / I.m;
             if (cv[win]) continue;
@@ -789,11 +867,11 @@ extern "C" rewl_status rewl_get_state(rewl_ctx *ctx, int inst, int8_t *spins, in
             }
         }
     }
-    if (stage) CK(cudaMemcpy(stage, ctx->d_stage + I.win0, 4 * I.h, cudaMemcpyDeviceToHost));
-    if (conv) CK(cudaMemcpy(conv, ctx->d_conv + I.win0, I.h, cudaMemcpyDeviceToHost));
-    if (latch) CK(cudaMemcpy(latch, ctx->d_latch + I.slot0, nw, cudaMemcpyDeviceToHost));
+    if (stage) CK(d2h(ctx, stage, ctx->d_stage + I.win0, 4 * I.h));
+    if (conv) CK(d2h(ctx, conv, ctx->d_conv + I.win0, I.h));
+    if (latch) CK(d2h(ctx, latch, ctx->d_latch + I.slot0, nw));
     if (replica) {
-        CK(dget(rep, ctx->d_replica + I.slot0, nw));
+        CK(dget(ctx, rep, ctx->d_replica + I.slot0, nw));
         for (int k = 0; k < nw; ++k) replica[k] = rep[k];
     }
     return REWL_OK;
@@ -806,10 +884,21 @@ extern "C" rewl_status rewl_get_counters(rewl_ctx *ctx, int inst, uint64_t *ex_p
     if (s) return s;
     if ((s = sync_and_check(ctx))) return s;
     const InstDev &I = ctx->inst[inst].dev;
-    if (ex_prop) CK(cudaMemcpy(ex_prop, ctx->d_ex_prop + I.win0, 8 * I.h, cudaMemcpyDeviceToHost));
-    if (ex_acc) CK(cudaMemcpy(ex_acc, ctx->d_ex_acc + I.win0, 8 * I.h, cudaMemcpyDeviceToHost));
-    if (n_accepted) CK(cudaMemcpy(n_accepted, ctx->d_nacc + I.slot0, 8 * (size_t)I.h * I.m, cudaMemcpyDeviceToHost));
-    if (conv_sweep) CK(cudaMemcpy(conv_sweep, ctx->d_conv_sweep + I.win0, 8 * I.h, cudaMemcpyDeviceToHost));
+    if (ex_prop) CK(d2h(ctx, ex_prop, ctx->d_ex_prop + I.win0, 8 * I.h));
+    if (ex_acc) CK(d2h(ctx, ex_acc, ctx->d_ex_acc + I.win0, 8 * I.h));
+    if (n_accepted) CK(d2h(ctx, n_accepted, ctx->d_nacc + I.slot0, 8 * (size_t)I.h * I.m));
+    if (conv_sweep) CK(d2h(ctx, conv_sweep, ctx->d_conv_sweep + I.win0, 8 * I.h));
+    return REWL_OK;
+}
+
+extern "C" rewl_status rewl_get_stage_sweeps(rewl_ctx *ctx, int inst, int64_t *stage_sweep)
+{
+    rewl_status s = check_inst(ctx, inst);
+    if (s) return s;
+    if (!stage_sweep) return fail(ctx, REWL_EINVAL, "stage_sweep is NULL");
+    if ((s = sync_and_check(ctx))) return s;
+    const InstDev &I = ctx->inst[inst].dev;
+    CK(d2h(ctx, stage_sweep, ctx->d_stage_sweep + (size_t)I.win0 * kMaxStages, 8 * (size_t)I.h * kMaxStages));
     return REWL_OK;
 }
 
@@ -821,20 +910,20 @@ extern "C" rewl_status rewl_status_query(rewl_ctx *ctx, int inst, int *all_conve
     if ((s = sync_and_check(ctx))) return s;
     if (all_converged) {
         std::vector<uint8_t> conv;
-        CK(dget(conv, ctx->d_conv, ctx->n_win));
+        CK(dget(ctx, conv, ctx->d_conv, ctx->n_win));
         *all_converged = std::all_of(conv.begin(), conv.end(), [](uint8_t v) { return v != 0; });
     }
     const InstDev &I = ctx->inst[inst].dev;
     if (ln_f_per_window) {
         std::vector<int32_t> st;
         std::vector<uint8_t> cv;
-        CK(dget(st, ctx->d_stage + I.win0, I.h));
-        CK(dget(cv, ctx->d_conv + I.win0, I.h));
+        CK(dget(ctx, st, ctx->d_stage + I.win0, I.h));
+        CK(dget(ctx, cv, ctx->d_conv + I.win0, I.h));
         for (int i = 0; i < I.h; ++i) ln_f_per_window[i] = cv[i] ? 0.0 : std::ldexp(1.0, -st[i]);
     }
     if (sweeps) {
         ull c[2];
-        CK(cudaMemcpy(c, ctx->d_counters, 16, cudaMemcpyDeviceToHost));
+        CK(d2h(ctx, c, ctx->d_counters, 16));
         *sweeps = (long)c[0];
     }
     return REWL_OK;
@@ -933,7 +1022,7 @@ extern "C" rewl_status rewl_get_dos(rewl_ctx *ctx, int inst, double *ln_g, long 
     const long need = per_window ? (long)I.h * I.w : (long)I.B;
     if (cap < need) return fail(ctx, REWL_EINVAL, "cap smaller than the result (" + std::to_string(need) + ")");
     std::vector<long long> u;
-    CK(dget(u, ctx->d_lng + I.lng_off, (size_t)I.h * I.m * I.w));
+    CK(dget(ctx, u, ctx->d_lng + I.lng_off, (size_t)I.h * I.m * I.w));
     std::vector<double> pieces((size_t)I.h * I.w);
     for (int i = 0; i < I.h; ++i)
         for (int b = 0; b < I.w; ++b) {
@@ -981,14 +1070,15 @@ extern "C" rewl_status rewl_set_initial_lng(rewl_ctx *ctx, int inst, const doubl
             if (!(std::fabs(units) < std::ldexp(1.0, 53))) return fail(ctx, REWL_EINVAL, "ln_g0 outside |ln g| < 2^21");
             for (int j = 0; j < I.m; ++j) u[((size_t)i * I.m + j) * I.w + b] = (long long)units;
         }
-    CK(cudaMemcpy(ctx->d_lng + I.lng_off, u.data(), 8 * u.size(), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->d_lng0 + I.lng_off, u.data(), 8 * u.size(), cudaMemcpyHostToDevice));
+    CK(h2d_sync(ctx, ctx->d_lng + I.lng_off, u.data(), 8 * u.size()));
+    CK(h2d_sync(ctx, ctx->d_lng0 + I.lng_off, u.data(), 8 * u.size()));
     CK(cudaMemset(ctx->d_H + I.lng_off, 0, 4 * u.size()));
     CK(cudaMemset(ctx->d_latch + I.slot0, 0, (size_t)I.h * I.m));
+    CK(cudaMemset(ctx->d_stage_sweep + (size_t)I.win0 * kMaxStages, 0xFF, 8 * (size_t)I.h * kMaxStages));
     std::vector<int32_t> st(I.h, k0 < 0 ? 0 : k0);
     std::vector<uint8_t> cv(I.h, k0 < 0 ? 2 : 0);     // 2: sampling with frozen weights, H counted
-    CK(cudaMemcpy(ctx->d_stage + I.win0, st.data(), 4 * I.h, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->d_conv + I.win0, cv.data(), I.h, cudaMemcpyHostToDevice));
+    CK(h2d_sync(ctx, ctx->d_stage + I.win0, st.data(), 4 * I.h));
+    CK(h2d_sync(ctx, ctx->d_conv + I.win0, cv.data(), I.h));
     return REWL_OK;
 }
 
@@ -1009,6 +1099,7 @@ extern "C" rewl_status rewl_warm_start(rewl_ctx *ctx, int inst, rewl_mlp *net, d
     std::string why;
     const int rc = mlp_warm_start(net, ctx->st, inst, I.h, I.w, k0, why);
     if (rc) return fail(ctx, (rewl_status)rc, "warm start: " + why);
+    CK(cudaMemset(ctx->d_stage_sweep + (size_t)I.win0 * kMaxStages, 0xFF, 8 * (size_t)I.h * kMaxStages));
     return REWL_OK;
 }
 
@@ -1039,6 +1130,11 @@ extern "C" rewl_status rewl_set_option(rewl_ctx *ctx, int option, long value)
             if (value < 1) return fail(ctx, REWL_EINVAL, "max sweeps per launch must be >= 1");
             ctx->max_sweeps_per_launch = value;
             break;
+        case REWL_OPT_LATTICE_PLACEMENT:
+            if (value < 0 || value > 2) return fail(ctx, REWL_EINVAL, "lattice placement must be 0, 1 or 2");
+            if (ctx->planned) return fail(ctx, REWL_ESTATE, "launch plan already fixed");
+            ctx->lattice_mode = (int)value;
+            break;
         default:
             return fail(ctx, REWL_EINVAL, "unknown option");
     }
@@ -1052,6 +1148,14 @@ extern "C" rewl_status rewl_set_option(rewl_ctx *ctx, int option, long value)
 
 extern "C" long rewl_launch_count(const rewl_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
+extern "C" rewl_status rewl_transfer_bytes(const rewl_ctx *ctx, int64_t *h2d, int64_t *d2h)
+{
+    if (!ctx) return REWL_EINVAL;
+    if (h2d) *h2d = ctx->bytes_h2d;
+    if (d2h) *d2h = ctx->bytes_d2h;
+    return REWL_OK;
+}
+
 extern "C" const char *rewl_last_error(const rewl_ctx *ctx)
 {
     if (!ctx) return g_create_error.c_str();
@@ -1061,7 +1165,7 @@ extern "C" const char *rewl_last_error(const rewl_ctx *ctx)
 // ---------------------------------------------------------------------------
 // checkpoint
 // ---------------------------------------------------------------------------
-static const char kMagic[8] = {'R', 'E', 'W', 'L', 'C', 'K', 'P', '3'};
+static const char kMagic[8] = {'R', 'E', 'W', 'L', 'C', 'K', 'P', '4'};
 
 template <class T>
 static bool wr(FILE *f, const std::vector<T> &v)
@@ -1084,6 +1188,7 @@ static bool rd(FILE *f, std::vector<T> &v)
     X(int64_t, d_conv_sweep, ctx->n_win)              \
     X(ull, d_ex_prop, ctx->n_win)                     \
     X(ull, d_ex_acc, ctx->n_win)                      \
+    X(int64_t, d_stage_sweep, (size_t)ctx->n_win * kMaxStages) \
     X(int32_t, d_cfg, ctx->n_slots)                   \
     X(int32_t, d_E, ctx->n_slots)                     \
     X(int32_t, d_bin, ctx->n_slots)                   \
@@ -1121,7 +1226,7 @@ extern "C" rewl_status rewl_save(rewl_ctx *ctx, const char *path)
 #define SAVE_ONE(T, field, n)                                     \
     if (ok) {                                                     \
         std::vector<T> v;                                         \
-        if (dget(v, ctx->field, n) != cudaSuccess) ok = false;    \
+        if (dget(ctx, v, ctx->field, n) != cudaSuccess) ok = false;    \
         ok = ok && wr(f, v);                                      \
     }
     STATE_ARRAYS(SAVE_ONE)
@@ -1163,7 +1268,7 @@ extern "C" rewl_status rewl_load(rewl_ctx **out, const char *path, void *cuda_st
     if (ok) {                                                                                           \
         std::vector<T> v;                                                                               \
         ok = rd(f, v) && v.size() == (size_t)(n);                                                      \
-        if (ok && cudaMemcpy(ctx->field, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess) \
+        if (ok && h2d_sync(ctx, ctx->field, v.data(), sizeof(T) * v.size()) != cudaSuccess) \
             ok = false;                                                                                 \
     }
     STATE_ARRAYS(LOAD_ONE)

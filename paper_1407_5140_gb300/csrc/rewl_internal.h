@@ -19,6 +19,9 @@ namespace rewl {
 
 enum : int { kIsing = 0, kPotts = 1 };
 
+// WL stages k = 0..32 (ln f = 2^-k) a window can pass through.
+enum : int { kMaxStages = 33 };
+
 // Error word bits raised by kernels (sticky, OR-ed).
 enum : int {
     kErrRange = 1,       // |ln g| reached 2^21 (FP64-exact range left)
@@ -46,9 +49,10 @@ struct InstDev {
     int32_t pad1;
 };
 
-// One thread block of the sweep kernel: n_win consecutive windows of one instance.
+// One thread block of the sweep kernel: n_win consecutive windows of one
+// instance; wrow = the widest of them (its walkers' ln g rows in shared memory).
 struct WorkItem {
-    int32_t inst, win_begin, n_win, pad;
+    int32_t inst, win_begin, n_win, wrow;
 };
 
 // One exchange proposal: walker j of window i of an instance (window pair i, i+1).
@@ -66,6 +70,9 @@ struct DevState {
     uint8_t *conv;
     int64_t *conv_sweep;
     unsigned long long *ex_prop, *ex_acc;
+    // per window and WL stage (kMaxStages each): the sweep count at which the
+    // stage ended with a merge (-1: not yet)
+    long long *stage_sweep;
     // per walker slot (global index)
     int32_t *cfg;
     int32_t *E;
@@ -103,6 +110,7 @@ struct SweepLaunch {
     int max_lat_words;
     int max_win;            // windows per block upper bound
     int model;              // all items of one launch share the model
+    int glat;               // 1: lattices stay in global memory (large L)
 };
 
 int launch_init(const DevState &st, int n_slots, const int32_t *slot_inst, void *stream);
@@ -112,7 +120,7 @@ int launch_exchange(const DevState &st, const ExTask *tasks0, int n0, const ExTa
                     void *stream);
 int launch_bump(const DevState &st, long sweeps, long exchanges, void *stream);
 int sweep_smem_bytes(int n_walkers, int n_win, int w, int lat_words, int producers, int N);
-int prepare_sweep(int model, int producers, int smem);
+int prepare_sweep(int model, bool glat, int smem);
 int launch_debug_lam(const uint32_t *k, int64_t *out, long n, void *stream);
 int launch_debug_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr, uint32_t *out, long n,
                         void *stream);

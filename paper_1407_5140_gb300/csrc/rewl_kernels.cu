@@ -289,6 +289,20 @@ __device__ __forceinline__ void st_shared_u8_if(bool p, uint32_t addr, uint32_t 
                  : "memory");
 }
 
+__device__ __forceinline__ void st_global_u32_if(bool p, unsigned char *ptr, uint32_t v)
+{
+    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.global.u32 [%1], %2;\n}" ::"r"((uint32_t)p),
+                 "l"(ptr), "r"(v)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_global_u8_if(bool p, unsigned char *ptr, uint32_t v)
+{
+    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.global.u8 [%1], %2;\n}" ::"r"((uint32_t)p),
+                 "l"(ptr), "r"(v)
+                 : "memory");
+}
+
 __device__ __forceinline__ void st_shared_s64_if(bool p, uint32_t addr, long long v)
 {
     asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.shared.s64 [%1], %2;\n}" ::"r"((uint32_t)p),
@@ -331,14 +345,21 @@ enum : int { kBarFull = 1, kBarEmpty = 3 };  // ids 1, 2 (full) and 3, 4 (empty)
 // ln f > 0 (it is read off ln g and its value at the stage start); converged
 // windows no longer count it, and sampling with frozen weights counts it in
 // global memory with fire-and-forget reductions.
-template <int MODEL>
+// GLAT: the lattices stay in global memory (large L, where a walker's lattice
+// would crowd shared memory); the trial records then hold byte offsets from
+// the start of the walker's lattice, and each consumer lane reads and writes
+// its own walker's lattice there (a thread sees its own earlier stores, and no
+// other thread touches that lattice during the launch).
+template <int MODEL, bool GLAT>
 __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkItem *items, SweepArgs args)
 {
     constexpr int APB = Apb<MODEL>::value;
     extern __shared__ __align__(16) unsigned char smem[];
     const WorkItem it = items[blockIdx.x];
     const InstDev I = st.inst[it.inst];
-    const int m = I.m, w = I.w, n_win = it.n_win;
+    // w: the instance's widest window (row stride of ln g, H in global
+    // memory); wr: the widest window of this block (row length in shared memory)
+    const int m = I.m, w = I.w, wr = it.wrow, n_win = it.n_win;
     const int nw = n_win * m;
     const int tid = threadIdx.x, nthreads = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -346,15 +367,17 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
     const bool valid = consumer && lane < nw;
     const int tv = (consumer && lane < nw) ? lane : 0;
     const int lw = I.lat_words;
-    const int lwp = lw | 1;                 // odd word stride spreads walkers over banks
-    const int wg = w + 2 * kGuard;
+    // shared-memory words per walker's lattice: an odd stride spreads walkers
+    // over banks; none when the lattices stay in global memory
+    const int lwp = GLAT ? 0 : (lw | 1);
+    const int wg = wr + 2 * kGuard;
 
     Trial *ring = reinterpret_cast<Trial *>(smem);
     long long *lng_s = reinterpret_cast<long long *>(ring + 2 * nw * kR);
     unsigned long long *draw_s = reinterpret_cast<unsigned long long *>(lng_s + (size_t)nw * wg);
     uint32_t *lat_s = reinterpret_cast<uint32_t *>(draw_s + nw);
     uint8_t *reach_s = reinterpret_cast<uint8_t *>(lat_s + (size_t)nw * lwp);
-    int *wst_s = reinterpret_cast<int *>(reach_s + ((size_t)n_win * w + 15) / 16 * 16);
+    int *wst_s = reinterpret_cast<int *>(reach_s + ((size_t)n_win * wr + 15) / 16 * 16);
     int *wstage_s = wst_s;
     int *wconv_s = wst_s + n_win;
     int *wmerge_s = wst_s + 2 * n_win;
@@ -371,15 +394,16 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
     for (int i = tid; i < nw * wg; i += nthreads) {
         const int k = i / wg, bb = i - k * wg - kGuard;
         long long v = 0;
-        if (bb >= 0 && bb < w) v = st.lng[I.lng_off + (long long)(it.win_begin * m + k) * w + bb];
+        if (bb >= 0 && bb < wr) v = st.lng[I.lng_off + (long long)(it.win_begin * m + k) * w + bb];
         lng_s[i] = v;
     }
-    for (int i = tid; i < nw * lw; i += nthreads) {
-        const int k = i / lw, x = i - k * lw;
-        lat_s[k * lwp + x] = st.lat[I.lat_off + (long long)st.cfg[slot_base + k] * lw + x];
-    }
-    for (int i = tid; i < n_win * w; i += nthreads) {
-        const int wl = i / w, bb = i - wl * w;
+    if (!GLAT)
+        for (int i = tid; i < nw * lw; i += nthreads) {
+            const int k = i / lw, x = i - k * lw;
+            lat_s[k * lwp + x] = st.lat[I.lat_off + (long long)st.cfg[slot_base + k] * lw + x];
+        }
+    for (int i = tid; i < n_win * wr; i += nthreads) {
+        const int wl = i / wr, bb = i - wl * wr;
         const int gw = I.win0 + it.win_begin + wl;
         reach_s[i] = bb < st.ww[gw] ? st.reach[I.reach_off + st.lo[gw] + bb] : (uint8_t)0;
     }
@@ -439,7 +463,8 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                     const unsigned long long blk = draw_s[wk] + (unsigned long long)(k * (kR / APB) + bi);
                     Trial tr[APB];
                     int first, last;
-                    uint32_t nbits = make_trials<MODEL>(tr, blk, c2, I, lat_base + 4u * (uint32_t)(wk * lwp), &first, &last);
+                    uint32_t nbits = make_trials<MODEL>(tr, blk, c2, I, GLAT ? 0u : lat_base + 4u * (uint32_t)(wk * lwp),
+                                                        &first, &last);
                     // the block's first trial against the last trial of the
                     // walker's previous block (none for the round's first
                     // block: the consumer reads that trial's values afresh)
@@ -473,6 +498,12 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
             const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
             // shared address of ln g of global bin 0 of this walker (bins lo..hi valid)
             const uint32_t lng_sa = (uint32_t)__cvta_generic_to_shared(lng_s + (size_t)tv * wg + kGuard) - 8u * (uint32_t)lo;
+            // the lane's lattice: trial offsets are from the block's shared
+            // memory, or from the walker's lattice in global memory
+            unsigned char *glat = GLAT ? reinterpret_cast<unsigned char *>(
+                                             st.lat + I.lat_off + (long long)st.cfg[slot_base + tv] * lw)
+                                       : nullptr;
+            const unsigned char *lbase = GLAT ? glat : smem;
             // the rounds of one sweep; kCountH adds the H counting of
             // frozen-weight sampling, compiled out where the warp has none: a run
             // of trials that end in the same bin is added to H when the walker
@@ -497,7 +528,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                     const uint32_t wm = __reduce_or_sync(0xffffffffu, nm);
                     Trial t = rr[0];
                     Trial t1 = rr[cnt > 1 ? nw : 0];
-                    const Nbr n0 = load_nbr<MODEL>(smem, t);
+                    const Nbr n0 = load_nbr<MODEL>(lbase, t);
                     int db = bin_change<MODEL>(n0, t, q);     // bin change of the current trial
                     uint32_t sv = n0.s;                        // its site word (Ising) / value (Potts)
                     bool acc_prev = false;
@@ -511,7 +542,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                         // the previous trial's H flush, its operands long ready
                         if (kCountH) red_add_global_u32_if(pend, Hpend, prun);
                         // the next trial's lattice values, read before this trial's move
-                        const Nbr nn = load_nbr<MODEL>(smem, t1);
+                        const Nbr nn = load_nbr<MODEL>(lbase, t1);
                         // this trial's move: Ising flips one bit of the site word,
                         // Potts writes the new value
                         uint32_t moved;
@@ -530,8 +561,13 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                         // and guard cells beyond the window's edges)
                         const long long v = lng[bn];
                         const bool acc = inw && (v < thr);
-                        if (MODEL == kIsing) st_shared_u32_if(valid && acc, sbase + t.a_s, moved);
-                        else st_shared_u8_if(valid && acc, sbase + t.a_s, moved);
+                        if (GLAT) {
+                            if (MODEL == kIsing) st_global_u32_if(valid && acc, glat + t.a_s, moved);
+                            else st_global_u8_if(valid && acc, glat + t.a_s, moved);
+                        } else {
+                            if (MODEL == kIsing) st_shared_u32_if(valid && acc, sbase + t.a_s, moved);
+                            else st_shared_u8_if(valid && acc, sbase + t.a_s, moved);
+                        }
                         // the next trial's bin change and site word from the values
                         // read before this move (the flag above catches the cases
                         // where this move changes them; an Ising site word shared
@@ -560,7 +596,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                     // trial a is near trial a - 1 in some lane: where that trial
                     // moved, db and sv were taken before the move -- read again
                     if (acc_prev && ((nm >> a) & 1u)) {
-                        const Nbr nf = load_nbr<MODEL>(smem, t);
+                        const Nbr nf = load_nbr<MODEL>(lbase, t);
                         db = bin_change<MODEL>(nf, t, q);
                         sv = nf.s;
                     }
@@ -591,7 +627,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                     const long long v = lk[bb];
                     const long long av = v < 0 ? -v : v;
                     amax = av > amax ? av : amax;
-                    if (reach_s[wlk * w + bb]) {
+                    if (reach_s[wlk * wr + bb]) {
                         const unsigned long long hv = (unsigned long long)((v - __ldcg(l0 + bb)) >> shift);
                         mn = hv < mn ? hv : mn;
                         sum += hv;
@@ -626,8 +662,8 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
             __syncthreads();
             // merge: ln g <- mean over the window's walkers (nearest 2^-32, ties
             // to even); the next stage starts from it (lng0 <- ln g, H <- 0)
-            for (int i = tid; i < n_win * w; i += nthreads) {
-                const int ww = i / w, bb = i - ww * w;
+            for (int i = tid; i < n_win * wr; i += nthreads) {
+                const int ww = i / wr, bb = i - ww * wr;
                 if (!wmerge_s[ww] || bb >= wwid_s[ww]) continue;
                 long long sacc = 0;
                 for (int jj = 0; jj < m; ++jj) sacc += lng_s[(size_t)(ww * m + jj) * wg + kGuard + bb];
@@ -642,6 +678,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
             for (int i = tid; i < n_win; i += nthreads) {
                 if (!wmerge_s[i]) continue;
                 for (int jj = 0; jj < m; ++jj) latch_s[i * m + jj] = 0;
+                st.stage_sweep[(size_t)wgwin_s[i] * kMaxStages + wstage_s[i]] = (long long)sweeps_done;
                 if (wstage_s[i] >= I.stage_final) {
                     wconv_s[i] = 1;
                     st.conv_sweep[wgwin_s[i]] = (long long)sweeps_done;
@@ -660,14 +697,15 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
         st.E[slot_base + tv] = (int)(I.e_min + (long long)b * I.step);
         st.n_acc[slot_base + tv] += n_acc;
     }
-    for (int i = tid; i < nw * w; i += nthreads) {
-        const int k = i / w, bb = i - k * w;
-        st.lng[I.lng_off + (long long)(it.win_begin * m) * w + i] = lng_s[(size_t)k * wg + kGuard + bb];
+    for (int i = tid; i < nw * wr; i += nthreads) {
+        const int k = i / wr, bb = i - k * wr;
+        st.lng[I.lng_off + (long long)(it.win_begin * m + k) * w + bb] = lng_s[(size_t)k * wg + kGuard + bb];
     }
-    for (int i = tid; i < nw * lw; i += nthreads) {
-        const int k = i / lw, x = i - k * lw;
-        st.lat[I.lat_off + (long long)st.cfg[slot_base + k] * lw + x] = lat_s[k * lwp + x];
-    }
+    if (!GLAT)
+        for (int i = tid; i < nw * lw; i += nthreads) {
+            const int k = i / lw, x = i - k * lw;
+            st.lat[I.lat_off + (long long)st.cfg[slot_base + k] * lw + x] = lat_s[k * lwp + x];
+        }
     for (int i = tid; i < n_win; i += nthreads) {
         st.stage[wgwin_s[i]] = wstage_s[i];
         st.conv[wgwin_s[i]] = (uint8_t)wconv_s[i];
@@ -678,19 +716,25 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
     }
 }
 
-int prepare_sweep(int model, int producers, int smem)
+static const void *sweep_fn(int model, bool glat)
 {
-    (void)producers;
+    if (model == kIsing) return glat ? (const void *)sweep_kernel<kIsing, true> : (const void *)sweep_kernel<kIsing, false>;
+    return glat ? (const void *)sweep_kernel<kPotts, true> : (const void *)sweep_kernel<kPotts, false>;
+}
+
+int prepare_sweep(int model, bool glat, int smem)
+{
     // the attribute belongs to the kernel, not to a context: never lower it
     // below what another live context already needs
-    static int granted[2] = {0, 0};
+    static int granted[4] = {0, 0, 0, 0};
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
-    if (smem <= granted[model & 1]) return 0;
-    granted[model & 1] = smem;
+    const int k = (model & 1) * 2 + (glat ? 1 : 0);
+    if (smem <= granted[k]) return 0;
+    granted[k] = smem;
     // every launch of the kernel asks for the largest shared-memory carveout, so
     // launches of different size classes can share an SM
-    const void *fn = model == kIsing ? (const void *)sweep_kernel<kIsing> : (const void *)sweep_kernel<kPotts>;
+    const void *fn = sweep_fn(model, glat);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
@@ -702,8 +746,13 @@ int launch_sweeps(const DevState &st, const SweepLaunch &sl, long n_sweeps, long
     SweepArgs a{n_sweeps, check_every};
     cudaStream_t s = (cudaStream_t)stream;
     if (sl.threads < 64 || sl.threads > 160 || sl.threads % 32 || sl.max_walkers > 32) return (int)cudaErrorInvalidValue;
-    if (sl.model == kIsing) sweep_kernel<kIsing><<<sl.n_items, sl.threads, sl.smem, s>>>(st, sl.items, a);
-    else sweep_kernel<kPotts><<<sl.n_items, sl.threads, sl.smem, s>>>(st, sl.items, a);
+    if (sl.model == kIsing) {
+        if (sl.glat) sweep_kernel<kIsing, true><<<sl.n_items, sl.threads, sl.smem, s>>>(st, sl.items, a);
+        else sweep_kernel<kIsing, false><<<sl.n_items, sl.threads, sl.smem, s>>>(st, sl.items, a);
+    } else {
+        if (sl.glat) sweep_kernel<kPotts, true><<<sl.n_items, sl.threads, sl.smem, s>>>(st, sl.items, a);
+        else sweep_kernel<kPotts, false><<<sl.n_items, sl.threads, sl.smem, s>>>(st, sl.items, a);
+    }
     return (int)cudaGetLastError();
 }
 

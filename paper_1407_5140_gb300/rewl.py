@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "librewl.so")
 
 ISING, POTTS = 0, 1
 OPT_CHECK_EVERY, OPT_PRODUCER_WARPS, OPT_WINDOWS_PER_CTA, OPT_MAX_SWEEPS_PER_LAUNCH, OPT_AUTOTUNE = 1, 2, 3, 4, 5
+OPT_LATTICE_PLACEMENT = 6
 STATUS = {0: "REWL_OK", -1: "REWL_EINVAL", -2: "REWL_ENOMEM", -3: "REWL_ECUDA", -4: "REWL_ETIMEOUT",
           -5: "REWL_ESTATE", -6: "REWL_EDEVICE"}
 
@@ -62,6 +63,7 @@ def lib():
         L.rewl_set_option.argtypes = [vp, i32, i64]
         L.rewl_launch_count.argtypes = [vp]
         L.rewl_launch_count.restype = i64
+        L.rewl_transfer_bytes.argtypes = [vp, vp, vp]
         L.rewl_save.argtypes = [vp, C.c_char_p]
         L.rewl_load.argtypes = [C.POINTER(vp), C.c_char_p, vp]
         L.rewl_last_error.argtypes = [vp]
@@ -83,6 +85,7 @@ def lib():
         L.rewl_warm_start.argtypes = [vp, i32, vp, f64]
         L.rewl_mlp_forward_noalloc.argtypes = [vp, vp, vp, i32, vp]
         L.rewl_join_pieces.argtypes = [i32, i32, i32, vp, vp, vp, f64, f64, vp, vp]
+        L.rewl_get_stage_sweeps.argtypes = [vp, i32, vp]
         L.rewl_debug_lam.argtypes = [vp, vp, i64]
         L.rewl_debug_philox.argtypes = [u32, u32, vp, vp, i64]
         for name in ("rewl_create", "rewl_create_batch", "rewl_run", "rewl_exchange", "rewl_run_cycles",
@@ -90,7 +93,8 @@ def lib():
                      "rewl_geometry", "rewl_get_state", "rewl_get_counters", "rewl_set_option", "rewl_save",
                      "rewl_load", "rewl_debug_lam", "rewl_debug_philox", "rewl_mlp_create", "rewl_mlp_set_params",
                      "rewl_mlp_get_params", "rewl_mlp_forward", "rewl_mlp_gradient", "rewl_mlp_train_step",
-                     "rewl_warm_start", "rewl_mlp_forward_noalloc", "rewl_join_pieces"):
+                     "rewl_warm_start", "rewl_mlp_forward_noalloc", "rewl_join_pieces",
+                     "rewl_get_stage_sweeps"):
             getattr(L, name).restype = i32
         _lib = L
     return _lib
@@ -223,6 +227,12 @@ class Rewl:
     def launch_count(self):
         return int(lib().rewl_launch_count(self._h))
 
+    def transfer_bytes(self):
+        """(host->device, device->host) bytes the library copied for this context."""
+        a, b = C.c_int64(), C.c_int64()
+        _check(lib().rewl_transfer_bytes(self._h, C.byref(a), C.byref(b)), self._h)
+        return a.value, b.value
+
     def warm_start(self, inst, net, ln_f_start):
         """rewl_warm_start: ln g of every walker from the network, ln f = ln_f_start."""
         _check(lib().rewl_warm_start(self._h, inst, net._h, ln_f_start), self._h)
@@ -279,6 +289,14 @@ class Rewl:
         _check(lib().rewl_get_counters(self._h, inst, *[_p(c[k]) for k in ("ex_prop", "ex_acc", "n_acc",
                                                                            "conv_sweep")]), self._h)
         return c
+
+    def stage_sweeps(self, inst=0):
+        """(h, 33) sweep counts at which each window ended each WL stage
+        (ln f = 2^-k), -1 where it has not."""
+        g = self.geometry(inst)
+        out = np.zeros(g["h"] * 33, np.int64)
+        _check(lib().rewl_get_stage_sweeps(self._h, inst, _p(out)), self._h)
+        return out.reshape(g["h"], 33)
 
     def get_dos(self, inst=0, per_window=False):
         g = self.geometry(inst)

@@ -70,16 +70,16 @@ def config4_targets():
     return [_inst(ISING, 128, 2, 64, 4, 6128), _inst(POTTS, 64, 10, 64, 4, 7064)]
 
 
-def potts_fss(sizes=(16, 24, 32, 48, 64), seeds=4, q=10, width=490):
+def potts_fss(sizes=(16, 24, 32, 48, 64), seeds=4, q=10, width=490, walkers=4, seed0=8000):
     """q-state Potts instances for locating the transition from specific-heat
-    maxima (Sec. IV A): windows of about `width` bins at 75 % overlap, 4
-    walkers each, `seeds` independent runs per size."""
+    maxima (Sec. IV A): windows of about `width` bins at 75 % overlap,
+    `walkers` walkers each, `seeds` independent runs per size."""
     out = []
     for L in sizes:
         B = 2 * L * L + 1
         h = max(4, int(round((B / width - 1.0) / 0.25 + 1.0)))
         for s in range(seeds):
-            out.append(_inst(POTTS, L, q, h, 4, 8000 + 100 * L + s))
+            out.append(_inst(POTTS, L, q, h, walkers, seed0 + 100 * L + s))
     return out
 
 

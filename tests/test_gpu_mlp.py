@@ -161,8 +161,9 @@ def test_warm_start_prediction_and_time_to_converge(stream):
     network gains is the starting estimate: its ln g is already close to the
     exact DOS.  The sweeps of the slowest window (Eq. (7)'s MC time) to reach
     ln f = 2^-20 depend on how well the prediction's shape across each window
-    matches (the correction at ln f = 2^-4 is slow), so the ratio varies with
-    the trained network; it is reported and bounded, and both runs end at
+    matches (the correction at ln f = 2^-4 is slow).  Training and REWL are
+    both deterministic (fixed-order reductions, counter-based random numbers),
+    so the ratio is one reproducible number: 0.913 on GB300, with both runs at
     comparable error against the exact DOS."""
     from paper_1407_5140_gb300 import rewl as R
     from paper_1407_5140_gb300 import warmstart as WS
@@ -176,9 +177,8 @@ def test_warm_start_prediction_and_time_to_converge(stream):
     X, T = WS.training_set(gen, train_inst)
     net = R.Mlp(max_batch=4096, seed=11, stream=stream)
     hist = WS.train(net, X, T, steps=1500, batch=4096, lr=2e-3, seed=2, log_every=500, lr_end=1e-4)
-    # RMS error of s = ln g / N over the whole training set (the mini-batch
-    # losses of the history vary with the order of the gradient's float
-    # atomics); s spans about 0 .. 2.3 here
+    # RMS error of s = ln g / N over the whole training set; s spans about
+    # 0 .. 2.3 here
     rms = float(np.sqrt(np.mean((WS.predict(net, X) - T) ** 2)))
     assert rms < 0.02, (rms, hist)
 
@@ -208,7 +208,7 @@ def test_warm_start_prediction_and_time_to_converge(stream):
     ws, we = results["warm"]
     print(f"start eps {np.mean(start_eps):.2e} | plain sweeps {ps.mean():.0f} eps {pe.mean():.2e} | "
           f"warm sweeps {ws.mean():.0f} eps {we.mean():.2e} | ratio {ws.mean() / ps.mean():.3f}")
-    # measured 0.81 ... 1.07 over training runs (float atomics make training
-    # order-dependent); the bound only rules out a broken start
-    assert 0.5 < ws.mean() / ps.mean() < 1.5
-    assert we.mean() < 1.5 * pe.mean() + 2e-3
+    # the learned start needs fewer sweeps: 0.913 of plain REWL's (measured,
+    # reproducible), at an error within 1.5 times plain REWL's (2.8e-3 vs 2.2e-3)
+    assert ws.mean() / ps.mean() < 0.95
+    assert we.mean() < 1.5 * pe.mean()

@@ -210,6 +210,50 @@ def test_extreme_sizes_match_oracle(name, d, sweeps, cycles):
         assert_same_state(gpu, 0, orc, f"{name} cycle {c}")
 
 
+GLOBAL_LATTICE = [
+    # 40 KB and 160 KB lattices (the paper's Potts L = 200 and 400) stay in
+    # global memory; energy sub-ranges keep the oracle's sweeps short
+    ("potts_q10_L200_sub", _potts(200, 10, 3, 2, seed=51, e_min=-60000, e_max=-59000), {}, 2, 2),
+    ("potts_q10_L400_sub", _potts(400, 10, 2, 1, seed=52, e_min=-200000, e_max=-199200), {}, 1, 2),
+    ("ising_L400_sub", _ising(400, 2, 2, seed=53, e_min=-200000, e_max=-198000), {}, 1, 2),
+    # global placement forced on lattices that would fit in shared memory
+    ("ising_L32_global", _ising(32, 8, 2, seed=54), {"lattice_placement": 1}, 6, 2),
+    ("potts_q10_L32_global", _potts(32, 10, 8, 2, seed=55), {"lattice_placement": 1}, 4, 2),
+    ("ising_L10_h3_m3_global", _ising(10, 3, 3, seed=47), {"lattice_placement": 1}, 40, 2),
+]
+
+
+@pytest.mark.parametrize("name,d,opts,sweeps,cycles", GLOBAL_LATTICE, ids=[c[0] for c in GLOBAL_LATTICE])
+def test_global_memory_lattices_match_oracle(name, d, opts, sweeps, cycles):
+    """The sweep kernel with the lattices left in global memory (large L):
+    bit-exact against the oracle."""
+    gpu = make_gpu([d], **opts)
+    orc = make_oracle(d)
+    orc.init()
+    assert_same_state(gpu, 0, orc, f"{name} after init")
+    for c in range(cycles):
+        step_both(gpu, [orc], sweeps)
+        assert_same_state(gpu, 0, orc, f"{name} cycle {c}")
+
+
+def test_lattice_placement_does_not_change_results():
+    """Potts L = 200 with its lattices in global memory (the default there)
+    and forced into shared memory: identical states after sweeps and
+    exchanges."""
+    d = _potts(200, 10, 4, 2, seed=56, e_min=-52000, e_max=-50500)
+    a = make_gpu([d])
+    b = make_gpu([d], lattice_placement=2)
+    for _ in range(2):
+        for g in (a, b):
+            g.run(2)
+            g.exchange()
+    sa, sb = a.state(0, 40000), b.state(0, 40000)
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+    with pytest.raises(Exception):
+        make_gpu([_potts(514, 10, 4, 1)])
+
+
 def test_learned_warm_start_install_then_bit_exact():
     """rewl_warm_start writes each walker's ln g from the network (window
     pieces shifted to a zero minimum), resets H and latches and sets the stage;
@@ -410,13 +454,33 @@ def test_potts_q10_full_convergence_invariants():
 
 def test_potts_q10_l32_config2_log_sum_invariant():
     # the q = 10, L = 32 workload (32 windows x 8 walkers) run to ln f = 2^-20:
-    # ln sum_E g(E) must be 1024 ln 10
+    # ln sum_E g(E) must be 1024 ln 10.  The bound, 0.7 in ln (3e-4 of 2358),
+    # is the spread of this sum over independent q = 10 runs at L = 16..64 to
+    # the same ln f; this seed's run gives 0.11.
     ds = W.config2()
     gpu = make_gpu(ds)
     assert gpu.run_to_convergence(1000, 3_000_000, poll_cycles=50)
     lg, _ = gpu.get_dos(0)
     from oracle.exact_dos import log_sum
     target = 1024 * math.log(10)
-    assert abs(log_sum(lg) - target) < 2e-3 * target, (log_sum(lg), target)
+    assert abs(log_sum(lg) - target) < 0.7, (log_sum(lg), target)
     c = gpu.counters(0)
     assert np.all(c["ex_acc"][:31] > 0)
+
+
+def test_transfer_bytes_count_every_copy():
+    # rewl_transfer_bytes: a read-out adds the 4-byte error word and the
+    # instance's h * m * w ln g values; a warm start adds ln g, its
+    # stage-start copy, stages and flags; neither moves bytes the other way
+    d = W.config0()[0]
+    gpu = make_gpu([d])
+    h2d0, d2h0 = gpu.transfer_bytes()
+    assert h2d0 > 0
+    g = gpu.geometry(0)
+    nbytes = g["h"] * g["m"] * g["w"] * 8
+    gpu.get_dos(0, per_window=True)
+    h2d1, d2h1 = gpu.transfer_bytes()
+    assert h2d1 == h2d0 and d2h1 - d2h0 == 4 + nbytes
+    gpu.set_initial_lng(0, np.zeros(g["B"]), 0.5)
+    h2d2, d2h2 = gpu.transfer_bytes()
+    assert h2d2 - h2d1 == 2 * nbytes + 4 * g["h"] + g["h"] and d2h2 - d2h1 == 4
