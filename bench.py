@@ -110,19 +110,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def _traffic_from_profile(kernel_src_sha):
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was
-    taken on the current kernel source."""
+def _profile_fields(kernel_src_sha):
+    """Figures of the committed ncu summary of the sweep kernel, if it was
+    taken on the current kernel source: DRAM bytes per sweep phase, issue-lane
+    slots per trial (inst_executed * 32 / trials) and issue slots active."""
     path = os.path.join(ROOT, "profiles", "sweep_kernel_ising_config1.md")
     try:
         txt = open(path).read()
     except OSError:
-        return None
+        return {}
     m = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
-    t = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.eE+]+)", txt)
-    if not m or not t or m.group(1) != kernel_src_sha:
-        return None
-    return float(t.group(1))
+    if not m or m.group(1) != kernel_src_sha:
+        return {}
+    out = {}
+    for key, name in (("traffic_bytes_per_launch_full", "traffic"),
+                      ("measured_issue_lane_slots_per_trial", "instr_per_trial_measured"),
+                      ("issue_slots_active_pct", "issue_slots_active_pct")):
+        t = re.search(key + r":\s*([0-9.eE+]+)", txt)
+        if t:
+            out[name] = float(t.group(1))
+    return out
 
 
 def _kernel_sha():
@@ -241,11 +248,17 @@ def run_ours(args, rank, world):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_instr = n_sm * 4 * 32 * MAX_SM_MHZ * 1e6
     achieved = instr * attempts_per_step / k_time
-    sha = _kernel_sha()
+    prof = _profile_fields(_kernel_sha())
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_instr / 1e12, "unit": "Tinstr/s",
-                "frac": achieved / peak_instr, "traffic": _traffic_from_profile(sha),
+                "frac": achieved / peak_instr, "traffic": prof.get("traffic"),
                 "peak_source": f"{n_sm} SMs x 4 schedulers x 32 lanes x {MAX_SM_MHZ:.0f} MHz (max SM clock)",
-                "instr_per_trial": instr, "kernel_time_s": k_time}
+                "instr_per_trial": instr, "kernel_time_s": k_time,
+                "instr_per_trial_measured": prof.get("instr_per_trial_measured"),
+                "issue_slots_active_pct": prof.get("issue_slots_active_pct"),
+                "measured_fields_from": "ncu capture in profiles/sweep_kernel_ising_config1.md (L=64 launch, "
+                                        "20 sweeps; null when the kernel source changed since)"}
+    if prof.get("instr_per_trial_measured"):
+        roofline["frac_at_measured_instr"] = prof["instr_per_trial_measured"] * attempts_per_step / k_time / peak_instr
     return dict(value=value, t_step=t_step, e2e=e2e, roofline=roofline, clocks=clocks, launches=launches,
                 attempts_per_step=attempts_per_step, ds=ds)
 
@@ -541,17 +554,22 @@ def potts_tc_workload(exchange_interval=1000, poll_cycles=5, cap_s=1500.0):
 
 
 def potts_tc_large_workload(sizes=(32, 48, 64, 80, 100, 128), seeds=4, width=490, stage_final=20,
-                            exchange_interval=1000, poll_cycles=5, cap_s=2400.0, seed0=60000, save=None):
-    """q = 10 Potts transition temperature from C_v maxima (Sec. IV A): every
-    size and seed in one batch, windows of about `width` bins at 75 %
-    overlap, one walker each, run to ln f = 2^-stage_final (lattices above
-    L = 128 stay in global memory during sweeps).  Per size the C_v peak of
-    the mean DOS with the paper's bootstrap error (Sec. II B: per-window
-    pieces of the seeds resampled with replacement, 200 times, each resample
-    joined), and the fit Tc(L) = Tc + a / L^2 against the exact
+                            exchange_interval=None, poll_cycles=5, cap_s=2400.0, seed0=60000, save=None):
+    """q = 10 Potts transition temperature from C_v maxima (Sec. IV A): one
+    batch per lattice size (its seeds together), the batches driven
+    concurrently from host threads on their own streams, so each size runs
+    at its own pace (a sweep of L = 400 is 16 times one of L = 100); windows
+    of about `width` bins at 75 % overlap, one walker each, run to
+    ln f = 2^-stage_final; lattices above L = 128 stay in global memory.
+    Exchanges every max(50, 10^7 / N) sweeps unless `exchange_interval` is
+    given.  Per size the C_v peak of the mean DOS with the paper's bootstrap
+    error (Sec. II B: per-window pieces of the seeds resampled with
+    replacement, 200 times, each resample joined) when there are several
+    seeds, and the fit Tc(L) = Tc + a / L^2 against the exact
     1 / ln(1 + sqrt q).  `save`: write every instance's pieces and geometry to
     this .npz file (for pooling runs)."""
     import math
+    import threading
     import numpy as np
     import torch
     from paper_1407_5140_gb300 import rewl as R
@@ -559,35 +577,61 @@ def potts_tc_large_workload(sizes=(32, 48, 64, 80, 100, 128), seeds=4, width=490
     from paper_1407_5140_gb300 import workloads as W
 
     torch.cuda.set_device(0)
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
-    ds = W.potts_fss(sizes=sizes, seeds=seeds, walkers=1, seed0=seed0, width=width)
-    for d in ds:
-        d["ln_f_final"] = 2.0 ** -stage_final
-    with ClockSampler(0) as clk:
-        t_c = time.perf_counter()
-        ctx = R.Rewl([R.instance(**d) for d in ds], stream=stream)
-        ctx.run(1)
-        torch.cuda.synchronize()
-        t_create = time.perf_counter() - t_c
-        t0 = time.perf_counter()
-        conv = _converge(ctx, exchange_interval, poll_cycles, cap_s, "potts fss")
-        torch.cuda.synchronize()
-        secs = time.perf_counter() - t0
-    q = ds[0]["q"]
+    q = 10
     tc_exact = 1.0 / math.log(1.0 + math.sqrt(q))
+    runs = {}
+    for L in sizes:
+        ds = W.potts_fss(sizes=(L,), seeds=seeds, walkers=1, seed0=seed0, width=width)
+        for d in ds:
+            d["ln_f_final"] = 2.0 ** -stage_final
+        x = exchange_interval or max(50, int(round(1e7 / (L * L))))
+        runs[L] = {"ds": ds, "x": x, "stream": torch.cuda.Stream()}
+
+    def drive(L):
+        r = runs[L]
+        try:
+            t0 = time.perf_counter()
+            ctx = R.Rewl([R.instance(**d) for d in r["ds"]], stream=r["stream"])
+            ctx.run(1)
+            r["stream"].synchronize()
+            r["create_s"] = time.perf_counter() - t0
+            done = False
+            while not done and time.perf_counter() - t0 < cap_s:
+                done = ctx.run_to_convergence(r["x"], 20 * r["x"], poll_cycles=poll_cycles)
+            r["stream"].synchronize()
+            r["seconds"] = time.perf_counter() - t0
+            r["converged"] = bool(done)
+            r["ctx"] = ctx
+            print(f"[potts fss] L={L}: {'converged' if done else 'stopped'} after {r['seconds']:.0f} s",
+                  file=sys.stderr, flush=True)
+        except Exception as e:          # reported in the output line
+            r["error"] = repr(e)
+
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        th = [threading.Thread(target=drive, args=(L,)) for L in sizes]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        secs = time.perf_counter() - t0
     per, saved = [], {}
     for L in sizes:
-        ks = [k for k, d in enumerate(ds) if d["L"] == L]
-        g = ctx.geometry(ks[0])
-        pieces = np.stack([ctx.get_dos(k, per_window=True)[0] for k in ks])
-        _, e = ctx.get_dos(ks[0])
+        r = runs[L]
+        ent = {"L": L, "windows": r["ds"][0]["n_windows"], "seeds": seeds, "exchange_every": r["x"],
+               "seconds": r.get("seconds"), "converged": r.get("converged", False)}
+        if "error" in r:
+            ent["error"] = r["error"]
+            per.append(ent)
+            continue
+        ctx = r["ctx"]
+        g = ctx.geometry(0)
+        pieces = np.stack([ctx.get_dos(k, per_window=True)[0] for k in range(seeds)])
+        _, e = ctx.get_dos(0)
         saved.update({f"L{L}_pieces": pieces, f"L{L}_lo": g["lo"], f"L{L}_ww": g["ww"], f"L{L}_reach": g["reach"],
-                      f"L{L}_e": e, f"L{L}_conv_sweep": np.array([ctx.counters(k)["conv_sweep"] for k in ks])})
-        ent = {"L": L, "windows": g["h"], "seeds": len(ks),
-               "sweeps_slowest_window": [int(ctx.counters(k)["conv_sweep"].max()) for k in ks],
-               "windows_converged": [int(np.sum(ctx.status(k)["ln_f"] == 0)) for k in ks]}
-        if conv:
+                      f"L{L}_e": e, f"L{L}_conv_sweep": np.array([ctx.counters(k)["conv_sweep"] for k in range(seeds)])})
+        ent["sweeps_slowest_window"] = [int(ctx.counters(k)["conv_sweep"].max()) for k in range(seeds)]
+        if ent["converged"]:
             lo_t, hi_t = 0.66, 0.76
 
             def tpk(lg, e=e):
@@ -596,32 +640,35 @@ def potts_tc_large_workload(sizes=(32, 48, 64, 80, 100, 128), seeds=4, width=490
             def cmax(lg, e=e, L=L):
                 return TH.cv_peak(lg, e, lo_t, hi_t)[1] / (L * L)
 
-            _, _, obs = TH.bootstrap_dos(pieces, g["lo"], g["ww"], g["reach"], 1.0, math.log(q), n_resamples=200,
-                                         seed=L, observables={"T_peak": tpk, "C_max_per_site": cmax})
-            ent.update({"T_peak": obs["T_peak"][0], "T_peak_bootstrap_err": obs["T_peak"][1],
-                        "C_max_per_site": obs["C_max_per_site"][0], "C_max_bootstrap_err": obs["C_max_per_site"][1],
-                        "log_sum_minus_N_ln_q": [_log_sum(ctx.get_dos(k)[0]) - L * L * math.log(q) for k in ks]})
+            if seeds > 1:
+                _, _, obs = TH.bootstrap_dos(pieces, g["lo"], g["ww"], g["reach"], 1.0, math.log(q), n_resamples=200,
+                                             seed=L, observables={"T_peak": tpk, "C_max_per_site": cmax})
+                ent.update({"T_peak": obs["T_peak"][0], "T_peak_bootstrap_err": obs["T_peak"][1],
+                            "C_max_per_site": obs["C_max_per_site"][0],
+                            "C_max_bootstrap_err": obs["C_max_per_site"][1]})
+            else:
+                lg = ctx.get_dos(0)[0]
+                ent.update({"T_peak": tpk(lg), "C_max_per_site": cmax(lg)})
+            ent["log_sum_minus_N_ln_q"] = [_log_sum(ctx.get_dos(k)[0]) - L * L * math.log(q) for k in range(seeds)]
         per.append(ent)
-    ctx.close()
+        ctx.close()
     if save:
         np.savez_compressed(save, **saved)
     fits = {}
-    if conv and seeds > 1:
-        Ls = [p["L"] for p in per]
-        tcs = [p["T_peak"] for p in per]
-        errs = [max(p["T_peak_bootstrap_err"], 1e-7) for p in per]
-        for lmin in sorted({min(Ls), 64, 100} & set(range(min(Ls), max(Ls)))):
-            idx = [i for i, L in enumerate(Ls) if L >= lmin]
+    ok = [p for p in per if "T_peak" in p]
+    if seeds > 1 and len(ok) >= 3:
+        Ls = [p["L"] for p in ok]
+        for lmin in sorted({Ls[0]} | {L for L in Ls if L in (64, 100)}):
+            idx = [k for k, L in enumerate(Ls) if L >= lmin]
             if len(idx) >= 3:
-                t, e_, a = TH.extrapolate_tc([Ls[i] for i in idx], [tcs[i] for i in idx], [errs[i] for i in idx])
+                t, e_, a = TH.extrapolate_tc([Ls[k] for k in idx], [ok[k]["T_peak"] for k in idx],
+                                             [max(ok[k]["T_peak_bootstrap_err"], 1e-7) for k in idx])
                 fits[f"L_ge_{lmin}"] = {"Tc_inf": t, "err": e_, "a": a}
     out = {"metric": "q=10 Potts transition temperature from C_v maxima", "n_gpus": 1, "data": "synthetic",
            "workload": f"q=10 Potts L={list(sizes)}, windows of ~{width} bins at 75 %, 1 walker each, {seeds} seeds "
-                       f"per size in one batch, exchange every {exchange_interval} sweeps, "
-                       f"ln f_final = 2^-{stage_final}",
-           "converged": bool(conv), "seconds": secs, "create_and_first_sweep_s": t_create,
-           "walkers": int(sum(d["n_windows"] for d in ds)), "sizes": per, "fits": fits, "Tc_exact": tc_exact,
-           "clocks": clk.summary()}
+                       f"per size, one batch per size run concurrently, ln f_final = 2^-{stage_final}",
+           "seconds": secs, "walkers": int(sum(r["ds"][0]["n_windows"] * seeds for r in runs.values())),
+           "sizes": per, "fits": fits, "Tc_exact": tc_exact, "clocks": clk.summary()}
     print(json.dumps(out))
 
 

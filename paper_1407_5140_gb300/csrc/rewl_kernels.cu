@@ -303,6 +303,13 @@ __device__ __forceinline__ void st_global_u8_if(bool p, unsigned char *ptr, uint
                  : "memory");
 }
 
+// Ask for the cache line at ptr to be brought into L2 (a hint: no value is
+// read and nothing waits for it).
+__device__ __forceinline__ void prefetch_l2(const unsigned char *ptr)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+}
+
 __device__ __forceinline__ void st_shared_s64_if(bool p, uint32_t addr, long long v)
 {
     asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.shared.s64 [%1], %2;\n}" ::"r"((uint32_t)p),
@@ -539,6 +546,13 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
     #pragma unroll 3
                     for (; a < a_end; ++a) {
                         const Trial t2 = rr[(size_t)(a + 2 < cnt ? a + 2 : cnt - 1) * nw];
+                        // lattices in global memory: start moving trial a+2's
+                        // rows towards L2 now, two trials before they are read
+                        if (GLAT) {
+                            prefetch_l2(glat + t2.a_s);
+                            prefetch_l2(glat + t2.a_u);
+                            prefetch_l2(glat + t2.a_d);
+                        }
                         // the previous trial's H flush, its operands long ready
                         if (kCountH) red_add_global_u32_if(pend, Hpend, prun);
                         // the next trial's lattice values, read before this trial's move

@@ -209,6 +209,6 @@ def test_warm_start_prediction_and_time_to_converge(stream):
     print(f"start eps {np.mean(start_eps):.2e} | plain sweeps {ps.mean():.0f} eps {pe.mean():.2e} | "
           f"warm sweeps {ws.mean():.0f} eps {we.mean():.2e} | ratio {ws.mean() / ps.mean():.3f}")
     # the learned start needs fewer sweeps: 0.913 of plain REWL's (measured,
-    # reproducible), at an error within 1.5 times plain REWL's (2.8e-3 vs 2.2e-3)
+    # reproducible), at an error 1.25 times plain REWL's (2.8e-3 vs 2.2e-3)
     assert ws.mean() / ps.mean() < 0.95
-    assert we.mean() < 1.5 * pe.mean()
+    assert we.mean() < 1.3 * pe.mean()
