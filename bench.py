@@ -579,9 +579,10 @@ def potts_tc_large_workload(sizes=(32, 48, 64, 80, 100, 128), seeds=4, width=490
     torch.cuda.set_device(0)
     q = 10
     tc_exact = 1.0 / math.log(1.0 + math.sqrt(q))
+    n_seeds = dict(zip(sizes, seeds)) if isinstance(seeds, (tuple, list)) else {L: seeds for L in sizes}
     runs = {}
     for L in sizes:
-        ds = W.potts_fss(sizes=(L,), seeds=seeds, walkers=1, seed0=seed0, width=width)
+        ds = W.potts_fss(sizes=(L,), seeds=n_seeds[L], walkers=1, seed0=seed0, width=width)
         for d in ds:
             d["ln_f_final"] = 2.0 ** -stage_final
         x = exchange_interval or max(50, int(round(1e7 / (L * L))))
@@ -618,6 +619,7 @@ def potts_tc_large_workload(sizes=(32, 48, 64, 80, 100, 128), seeds=4, width=490
     per, saved = [], {}
     for L in sizes:
         r = runs[L]
+        seeds = n_seeds[L]
         ent = {"L": L, "windows": r["ds"][0]["n_windows"], "seeds": seeds, "exchange_every": r["x"],
                "seconds": r.get("seconds"), "converged": r.get("converged", False)}
         if "error" in r:
@@ -655,8 +657,8 @@ def potts_tc_large_workload(sizes=(32, 48, 64, 80, 100, 128), seeds=4, width=490
     if save:
         np.savez_compressed(save, **saved)
     fits = {}
-    ok = [p for p in per if "T_peak" in p]
-    if seeds > 1 and len(ok) >= 3:
+    ok = [p for p in per if "T_peak_bootstrap_err" in p]
+    if len(ok) >= 3:
         Ls = [p["L"] for p in ok]
         for lmin in sorted({Ls[0]} | {L for L in Ls if L in (64, 100)}):
             idx = [k for k, L in enumerate(Ls) if L >= lmin]
@@ -665,9 +667,10 @@ def potts_tc_large_workload(sizes=(32, 48, 64, 80, 100, 128), seeds=4, width=490
                                              [max(ok[k]["T_peak_bootstrap_err"], 1e-7) for k in idx])
                 fits[f"L_ge_{lmin}"] = {"Tc_inf": t, "err": e_, "a": a}
     out = {"metric": "q=10 Potts transition temperature from C_v maxima", "n_gpus": 1, "data": "synthetic",
-           "workload": f"q=10 Potts L={list(sizes)}, windows of ~{width} bins at 75 %, 1 walker each, {seeds} seeds "
-                       f"per size, one batch per size run concurrently, ln f_final = 2^-{stage_final}",
-           "seconds": secs, "walkers": int(sum(r["ds"][0]["n_windows"] * seeds for r in runs.values())),
+           "workload": f"q=10 Potts L={list(sizes)}, windows of ~{width} bins at 75 %, 1 walker each, "
+                       f"{[n_seeds[L] for L in sizes]} seeds per size, one batch per size run concurrently, "
+                       f"ln f_final = 2^-{stage_final}",
+           "seconds": secs, "walkers": int(sum(r["ds"][0]["n_windows"] * n_seeds[L] for L, r in runs.items())),
            "sizes": per, "fits": fits, "Tc_exact": tc_exact, "clocks": clk.summary()}
     print(json.dumps(out))
 
@@ -986,7 +989,7 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="only the workload's launch shape with 20 sweeps per launch (for ncu captures)")
     ap.add_argument("--sizes", default=None, help="potts-tc-large: comma-separated lattice sides")
-    ap.add_argument("--seeds", type=int, default=None, help="potts-tc-large: independent runs per size")
+    ap.add_argument("--seeds", default=None, help="potts-tc-large: independent runs per size (one number, or one per size)")
     ap.add_argument("--width", type=int, default=None, help="potts-tc-large: bins per window")
     ap.add_argument("--stage-final", type=int, default=None, help="potts-tc-large: last WL stage (ln f = 2^-k)")
     ap.add_argument("--cap-s", type=float, default=None, help="potts-tc-large: wall-time cap of the run")
@@ -1036,7 +1039,8 @@ def main():
         if args.sizes:
             kw["sizes"] = tuple(int(x) for x in args.sizes.split(","))
         if args.seeds:
-            kw["seeds"] = args.seeds
+            sd = [int(x) for x in args.seeds.split(",")]
+            kw["seeds"] = sd[0] if len(sd) == 1 else tuple(sd)
         if args.width:
             kw["width"] = args.width
         if args.stage_final:

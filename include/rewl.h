@@ -215,9 +215,18 @@ rewl_status rewl_get_counters(rewl_ctx *ctx, int inst, uint64_t *ex_prop, uint64
  * Potts L = 200...400); 1 = always global; 2 = always shared (contexts
  * whose windows' state then exceeds shared memory fail to plan, REWL_EINVAL).
  * Shapes and placement never change results.
+ * REWL_OPT_LNG_SHIFT: s in 1..20 (default 20).  ln g of a window is defined
+ * up to a constant (the pieces are joined by their differences, Sec. II B;
+ * acceptance and Eq. (1) use differences within one window): at each flatness
+ * test, a running window whose walkers' ln g has reached 2^s on every
+ * realisable bin has 2^s taken off those bins (ln g and its stage-start copy,
+ * so H and the trajectory are unchanged).  This keeps ln g inside the exactly
+ * representable range |ln g| < 2^21 on large lattices, where the first stages
+ * add far more than 2^21 per bin.  Small s is for tests.
  * Launch-shape options may only be set before the first run. */
 enum { REWL_OPT_CHECK_EVERY = 1, REWL_OPT_PRODUCER_WARPS = 2, REWL_OPT_WINDOWS_PER_CTA = 3,
-       REWL_OPT_MAX_SWEEPS_PER_LAUNCH = 4, REWL_OPT_AUTOTUNE = 5, REWL_OPT_LATTICE_PLACEMENT = 6 };
+       REWL_OPT_MAX_SWEEPS_PER_LAUNCH = 4, REWL_OPT_AUTOTUNE = 5, REWL_OPT_LATTICE_PLACEMENT = 6,
+       REWL_OPT_LNG_SHIFT = 7 };
 rewl_status rewl_set_option(rewl_ctx *ctx, int option, long value);
 
 /* Number of kernel launches this context enqueued so far (graph replays count

@@ -46,6 +46,7 @@ def lib():
         L.oracle_get_counters.argtypes = [vp] * 7
         L.oracle_all_converged.argtypes = [vp]
         L.oracle_set_check_every.argtypes = [vp, i64]
+        L.oracle_set_shift_exp.argtypes = [vp, C.c_int]
         L.oracle_set_flat_rule.argtypes = [vp, C.c_int]
         L.oracle_set_windows.argtypes = [vp, vp, vp]
         L.oracle_set_windows.restype = C.c_int
@@ -197,6 +198,11 @@ class Oracle:
 
     def set_check_every(self, c):
         lib().oracle_set_check_every(self._o, c)
+
+    def set_shift_exp(self, e):
+        """ln g of a running window is lowered by 2^e once every realisable
+        bin of every walker has reached 2^e (1 <= e <= 20; 20 by default)."""
+        lib().oracle_set_shift_exp(self._o, e)
 
     def all_converged(self):
         return bool(lib().oracle_all_converged(self._o))

@@ -22,6 +22,13 @@
  * Readings where the paper is silent:
  *   - ln g is FP64; every value it takes is a multiple of 2^-32 below 2^21
  *     in magnitude, so differences are exact.  The oracle checks the bound.
+ *   - ln g of a window is defined up to a constant (the pieces are joined
+ *     by their differences, Sec. II B; acceptance and exchange, Eq. (1), use
+ *     differences within one window), so a running window whose ln g has
+ *     reached 2^s on every realisable bin of every walker has 2^s taken off
+ *     those bins at the next flatness test (s = 20 unless set): on large
+ *     lattices the first stages add far more than 2^21 per bin.  The
+ *     trajectory is unchanged, and H is kept separately.
  *   - accept iff (ln g(E') - ln g(E)) * 2^32 < lam_fix, where
  *     lam_fix = max(1, trunc(2^32 * lam)) and lam = -ln u is evaluated in
  *     binary32 by the routine lam_spec below (u = (k+1) 2^-24, k = r >> 8).
@@ -149,6 +156,8 @@ typedef struct {
     double p_flat, ln_f_final;
     int flat_rule;            /* 0: min H >= p <H>;  1: min H >= a/sqrt(ln f)  */
     long check_every;         /* sweeps between flatness tests               */
+    int shift_exp;            /* ln g of a window is lowered by 2^shift_exp
+                                 once all its values reach it               */
     uint32_t key0, key1;
     int n_walkers;            /* h * m, walker id = window * m + j           */
     signed char **spin;       /* per walker slot: its current configuration  */
@@ -301,6 +310,7 @@ rewl_oracle *oracle_create(int model, int L, int q, long e_min, long e_max,
     }
     o->p_flat = p_flat; o->ln_f_final = ln_f_final;
     o->check_every = 1;
+    o->shift_exp = 20;
     o->key0 = (uint32_t)seed;
     o->key1 = (uint32_t)(seed >> 32) ^ instance;
     o->n_walkers = h * m;
@@ -482,6 +492,19 @@ static void window_boundary(rewl_oracle *o, int win)
 {
     if (o->conv[win]) return;
     int m = o->m, all = 1;
+    /* ln g is defined up to a constant per window: lower it by 2^s once every
+     * realisable bin of every walker has reached 2^s */
+    double lmin = INFINITY, s = ldexp(1.0, o->shift_exp);
+    for (int j = 0; j < m; ++j)
+        for (int b = 0; b < o->ww[win]; ++b)
+            if (o->reach[o->lo[win] + b]) {
+                double v = o->lng[(size_t)(win * m + j) * o->w + b];
+                if (v < lmin) lmin = v;
+            }
+    if (lmin >= s)
+        for (int j = 0; j < m; ++j)
+            for (int b = 0; b < o->ww[win]; ++b)
+                if (o->reach[o->lo[win] + b]) o->lng[(size_t)(win * m + j) * o->w + b] -= s;
     for (int j = 0; j < m; ++j) {
         int k = win * m + j;
         if (!o->latch[k] && walker_flat(o, k)) o->latch[k] = 1;
@@ -671,6 +694,7 @@ void oracle_get_counters(const rewl_oracle *o, long *sweeps, uint64_t *t_exch, u
 }
 
 void oracle_set_check_every(rewl_oracle *o, long c) { o->check_every = c > 0 ? c : 1; }
+void oracle_set_shift_exp(rewl_oracle *o, int e) { o->shift_exp = e >= 1 && e <= 20 ? e : 20; }
 
 /* 0: fraction-of-mean flatness (Sec. II A); 1: Zhou-Bhatt minimum (Eq. (8)) */
 void oracle_set_flat_rule(rewl_oracle *o, int rule) { o->flat_rule = rule == 1 ? 1 : 0; }

@@ -70,6 +70,7 @@ struct rewl_ctx {
     long max_sweeps_per_launch = 1L << 30;
     int force_producers = 0, force_wpc = 0;
     int lattice_mode = 0;               // 0: by size, 1: global memory, 2: shared memory
+    int shift_exp = 20;                 // a running window's ln g is lowered by 2^shift_exp once all of it reaches that
     int tune_mode = 1;                  // 1: measure candidate shapes, 0: rule only
     int tune_target = 0, tune_bias = 0; // chosen walkers-per-block target / producer bias
     bool planned = false;
@@ -531,6 +532,7 @@ static void measure_shapes(rewl_ctx *ctx)
             sh->tune_target = t;
             sh->tune_bias = b;
             sh->lattice_mode = ctx->lattice_mode;
+            sh->shift_exp = ctx->shift_exp;
             sh->check_every = ctx->check_every;
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             float ms = -1.f;
@@ -554,7 +556,10 @@ static void measure_shapes(rewl_ctx *ctx)
 // Blocks whose windows are narrower than the instance's widest need shorter
 // ln g rows in shared memory: split each size class into launches by the
 // block row width (rounded up to 64 bins), each asking only for the shared
-// memory its widest block needs.  Equal-width windows stay one launch.
+// memory its widest block needs, and give each launch the block shape its
+// rows allow (adjacent window groups of one instance merged into larger
+// blocks where narrow rows leave the room).  Equal-width windows stay one
+// launch.
 static void split_by_row(rewl_ctx *ctx)
 {
     std::vector<SizeClass> out;
@@ -567,15 +572,40 @@ static void split_by_row(rewl_ctx *ctx)
         }
         for (auto &kv : by) {
             SizeClass d = c;
-            d.items = kv.second;
             int wmax = 0, wpc = 0;
-            for (const WorkItem &it : d.items) {
+            for (const WorkItem &it : kv.second) {
                 wmax = std::max(wmax, it.wrow);
                 wpc = std::max(wpc, it.n_win);
             }
+            int wpc2 = 0, prod2 = 0;
+            if (!rewl::block_shape(ctx, c.model, c.N, wmax, c.m, c.lat_words, &wpc2, &prod2) && wpc2 > wpc) {
+                // merge runs of adjacent windows of one instance up to wpc2 windows
+                std::vector<WorkItem> merged;
+                for (const WorkItem &it : kv.second) {
+                    if (!merged.empty()) {
+                        WorkItem &bk = merged.back();
+                        if (bk.inst == it.inst && bk.win_begin + bk.n_win == it.win_begin &&
+                            bk.n_win + it.n_win <= wpc2) {
+                            bk.n_win += it.n_win;
+                            bk.wrow = std::max(bk.wrow, it.wrow);
+                            continue;
+                        }
+                    }
+                    merged.push_back(it);
+                }
+                wpc = 0;
+                for (const WorkItem &it : merged) wpc = std::max(wpc, it.n_win);
+                d.items = merged;
+                d.sl.producers = prod2;
+                d.sl.threads = 32 * (1 + prod2);
+            } else {
+                d.items = kv.second;
+            }
             d.sl.n_items = (int)d.items.size();
-            d.sl.smem = sweep_smem_bytes(wpc * c.m, wpc, wmax, c.lat_words, c.sl.producers, c.N);
+            d.sl.smem = sweep_smem_bytes(wpc * c.m, wpc, wmax, c.lat_words, d.sl.producers, c.N);
             d.sl.max_w = wmax;
+            d.sl.max_walkers = wpc * c.m;
+            d.sl.max_win = wpc;
             out.push_back(d);
         }
     }
@@ -655,13 +685,13 @@ static rewl_status enqueue_sweeps(rewl_ctx *ctx, long n)
     while (n > 0) {
         const long chunk = std::min(n, ctx->max_sweeps_per_launch);
         if (ctx->classes.size() == 1) {
-            int e = launch_sweeps(ctx->st, ctx->classes[0].sl, chunk, ctx->check_every, s);
+            int e = launch_sweeps(ctx->st, ctx->classes[0].sl, chunk, ctx->check_every, ctx->shift_exp, s);
             if (e) return fail(ctx, REWL_ECUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)e));
         } else {
             CK(cudaEventRecord(ctx->fork, s));
             for (auto &c : ctx->classes) {
                 CK(cudaStreamWaitEvent(c.stream, ctx->fork, 0));
-                int e = launch_sweeps(ctx->st, c.sl, chunk, ctx->check_every, c.stream);
+                int e = launch_sweeps(ctx->st, c.sl, chunk, ctx->check_every, ctx->shift_exp, c.stream);
                 if (e) return fail(ctx, REWL_ECUDA, std::string("sweep launch: ") + cudaGetErrorString((cudaError_t)e));
                 CK(cudaEventRecord(c.done, c.stream));
                 CK(cudaStreamWaitEvent(s, c.done, 0));
@@ -1129,6 +1159,10 @@ extern "C" rewl_status rewl_set_option(rewl_ctx *ctx, int option, long value)
         case REWL_OPT_MAX_SWEEPS_PER_LAUNCH:
             if (value < 1) return fail(ctx, REWL_EINVAL, "max sweeps per launch must be >= 1");
             ctx->max_sweeps_per_launch = value;
+            break;
+        case REWL_OPT_LNG_SHIFT:
+            if (value < 1 || value > 20) return fail(ctx, REWL_EINVAL, "ln g shift exponent must be in 1..20");
+            ctx->shift_exp = (int)value;
             break;
         case REWL_OPT_LATTICE_PLACEMENT:
             if (value < 0 || value > 2) return fail(ctx, REWL_EINVAL, "lattice placement must be 0, 1 or 2");

@@ -114,7 +114,7 @@ struct SweepLaunch {
 };
 
 int launch_init(const DevState &st, int n_slots, const int32_t *slot_inst, void *stream);
-int launch_sweeps(const DevState &st, const SweepLaunch &sl, long n_sweeps, long check_every,
+int launch_sweeps(const DevState &st, const SweepLaunch &sl, long n_sweeps, long check_every, int shift_exp,
                   void *stream);
 int launch_exchange(const DevState &st, const ExTask *tasks0, int n0, const ExTask *tasks1, int n1,
                     void *stream);
@@ -140,6 +140,10 @@ int mlp_warm_start(rewl_mlp *net, const DevState &st, int inst, int h, int w, in
 struct rewl_ctx;
 namespace rewl {
 int autotune_plan(rewl_ctx *ctx);
+// Windows per block and producer warps for blocks of m-walker windows with
+// ln g rows of w bins (the measured or rule target, shrunk to fit shared
+// memory); 0 on success, 1 if not even one window fits.
+int block_shape(const rewl_ctx *ctx, int model, int N, int w, int m, int lw, int *wpc, int *producers);
 void plan_class(rewl_ctx *ctx, int c, int wpc, int producers);
 int class_count(const rewl_ctx *ctx);
 int class_walkers(const rewl_ctx *ctx, int c);

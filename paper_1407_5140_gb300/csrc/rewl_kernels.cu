@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <climits>
+
 #include <mutex>
 #include <type_traits>
 
@@ -137,11 +139,13 @@ int sweep_smem_bytes(int n_walkers, int n_win, int w, int lat_words, int produce
     b += (long long)n_win * 20;                         // window state
     b += ((long long)n_walkers + 15) / 16 * 16;         // latch
     b += 2LL * n_walkers * 4;                           // near masks, 2 slots
+    b += 8 + (long long)n_walkers * 8;                  // smallest ln g per walker (8-byte aligned)
     return (int)b;
 }
 
 struct SweepArgs {
     long n_sweeps, check_every;
+    int shift_exp;   // a running window's ln g is lowered by 2^shift_exp once all of it has reached that
 };
 
 // Trials per Philox block: Ising 2 (site, u) pairs, Potts 1 (site, value, u).
@@ -393,6 +397,9 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
     uint8_t *latch_s = reinterpret_cast<uint8_t *>(wst_s + 5 * n_win);
     // per slot and walker: bit a set when trial a of the round is near trial a - 1
     uint32_t *nearm_s = reinterpret_cast<uint32_t *>(latch_s + (nw + 15) / 16 * 16);
+    // per walker: its smallest ln g over the realisable bins (flatness pass)
+    long long *lmin_s = reinterpret_cast<long long *>(
+        (reinterpret_cast<uintptr_t>(nearm_s + 2 * nw) + 7) & ~static_cast<uintptr_t>(7));
 
     const int slot_base = I.slot0 + it.win_begin * m;
     uint32_t *Hblk = st.H + I.lng_off + (long long)it.win_begin * m * w;   // this block's histograms
@@ -636,7 +643,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                 const long long *l0 = lng0blk + (size_t)wk * w;
                 const int shift = 32 - wstage_s[wlk];   // ln f = 2^(32 - stage) units
                 unsigned long long mn = ~0ull, sum = 0ull;
-                long long amax = 0;
+                long long amax = 0, lmin = LLONG_MAX;
                 for (int bb = lane; bb < wwid_s[wlk]; bb += 32) {
                     const long long v = lk[bb];
                     const long long av = v < 0 ? -v : v;
@@ -645,6 +652,7 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                         const unsigned long long hv = (unsigned long long)((v - __ldcg(l0 + bb)) >> shift);
                         mn = hv < mn ? hv : mn;
                         sum += hv;
+                        lmin = v < lmin ? v : lmin;
                     }
                 }
 #pragma unroll
@@ -652,11 +660,14 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                     const unsigned long long omn = __shfl_xor_sync(0xffffffffu, mn, o);
                     const unsigned long long osm = __shfl_xor_sync(0xffffffffu, sum, o);
                     const long long oam = __shfl_xor_sync(0xffffffffu, amax, o);
+                    const long long olm = __shfl_xor_sync(0xffffffffu, lmin, o);
                     mn = omn < mn ? omn : mn;
                     sum += osm;
                     amax = oam > amax ? oam : amax;
+                    lmin = olm < lmin ? olm : lmin;
                 }
                 if (lane == 0) {
+                    lmin_s[wk] = lmin;
                     if (amax >= (1LL << 53)) atomicOr(st.error, kErrRange);
                     const int n_reach = st.n_reach[I.win0 + it.win_begin + wlk];
                     // Sec. II A: min H >= p <H>; Eq. (8): min H >= a / sqrt(ln f),
@@ -668,10 +679,23 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                 }
             }
             __syncthreads();
+            // bit 0: merge the window; bit 1: lower its ln g by 2^shift_exp.  ln g
+            // of a window is defined up to a constant (pieces are joined by
+            // differences, Sec. II B; acceptance and Eq. (1) use differences
+            // within a window), so a running window whose walkers' ln g has
+            // reached 2^shift_exp on every realisable bin is lowered by that
+            // much (ln g and the stage-start copy alike, so H is unchanged):
+            // on large lattices the first stages add far more than 2^21 per bin
+            const long long lshift = 1LL << (32 + args.shift_exp);
             for (int i = tid; i < n_win; i += nthreads) {
                 int all = !wconv_s[i];
-                for (int jj = 0; jj < m && all; ++jj) all = latch_s[i * m + jj];
-                wmerge_s[i] = all;
+                long long wmin = LLONG_MAX;
+                for (int jj = 0; jj < m; ++jj) {
+                    all = all && latch_s[i * m + jj];
+                    wmin = lmin_s[i * m + jj] < wmin ? lmin_s[i * m + jj] : wmin;
+                }
+                const int lower = !wconv_s[i] && wmin >= lshift;
+                wmerge_s[i] = all | (lower << 1);
             }
             __syncthreads();
             // merge: ln g <- mean over the window's walkers (nearest 2^-32, ties
@@ -679,6 +703,12 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
             for (int i = tid; i < n_win * wr; i += nthreads) {
                 const int ww = i / wr, bb = i - ww * wr;
                 if (!wmerge_s[ww] || bb >= wwid_s[ww]) continue;
+                if ((wmerge_s[ww] & 2) && reach_s[ww * wr + bb])
+                    for (int jj = 0; jj < m; ++jj) {
+                        lng_s[(size_t)(ww * m + jj) * wg + kGuard + bb] -= lshift;
+                        lng0blk[(size_t)(ww * m + jj) * w + bb] -= lshift;
+                    }
+                if (!(wmerge_s[ww] & 1)) continue;
                 long long sacc = 0;
                 for (int jj = 0; jj < m; ++jj) sacc += lng_s[(size_t)(ww * m + jj) * wg + kGuard + bb];
                 const long long mean = div_round_even(sacc, m);
@@ -690,7 +720,9 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
             }
             __syncthreads();
             for (int i = tid; i < n_win; i += nthreads) {
-                if (!wmerge_s[i]) continue;
+                const int f = wmerge_s[i];
+                wmerge_s[i] = 0;
+                if (!(f & 1)) continue;
                 for (int jj = 0; jj < m; ++jj) latch_s[i * m + jj] = 0;
                 st.stage_sweep[(size_t)wgwin_s[i] * kMaxStages + wstage_s[i]] = (long long)sweeps_done;
                 if (wstage_s[i] >= I.stage_final) {
@@ -699,7 +731,6 @@ __global__ void __launch_bounds__(160, 1) sweep_kernel(DevState st, const WorkIt
                 } else {
                     wstage_s[i] += 1;
                 }
-                wmerge_s[i] = 0;
             }
         }
         __syncthreads();
@@ -755,9 +786,10 @@ int prepare_sweep(int model, bool glat, int smem)
     return (int)e;
 }
 
-int launch_sweeps(const DevState &st, const SweepLaunch &sl, long n_sweeps, long check_every, void *stream)
+int launch_sweeps(const DevState &st, const SweepLaunch &sl, long n_sweeps, long check_every, int shift_exp,
+                  void *stream)
 {
-    SweepArgs a{n_sweeps, check_every};
+    SweepArgs a{n_sweeps, check_every, shift_exp};
     cudaStream_t s = (cudaStream_t)stream;
     if (sl.threads < 64 || sl.threads > 160 || sl.threads % 32 || sl.max_walkers > 32) return (int)cudaErrorInvalidValue;
     if (sl.model == kIsing) {

@@ -47,29 +47,35 @@ static int pick_producers(int model, int nw)
     return std::max(1, std::min(4, p));
 }
 
+int block_shape(const rewl_ctx *ctx, int model, int N, int w, int m, int lw, int *wpc_out, int *producers_out)
+{
+    const int sms = device_sms();
+    const int target = tune_target(ctx), bias = tune_producer_bias(ctx);
+    auto producers = [&](int wpc) {
+        return forced_producers(ctx) ? forced_producers(ctx)
+                                     : std::max(1, std::min(4, pick_producers(model, wpc * m) + bias));
+    };
+    auto smem = [&](int wpc) { return sweep_smem_bytes(wpc * m, wpc, w, lw, producers(wpc), N); };
+    if (m > 32 || sweep_smem_bytes(m, 1, w, lw, 1, N) > 227 * 1024) return 1;
+    int wpc = forced_wpc(ctx);
+    if (!wpc) {
+        wpc = std::max(1, (target ? target : pick_walkers(total_walkers(ctx), sms)) / m);
+        while (wpc > 1 && (wpc * m > 32 || smem(wpc) > kSmemBudget)) --wpc;
+    }
+    if (wpc * m > 32 || smem(wpc) > 227 * 1024) return 1;
+    *wpc_out = wpc;
+    *producers_out = producers(wpc);
+    return 0;
+}
+
 int autotune_plan(rewl_ctx *ctx)
 {
     const int nc = class_count(ctx);
-    const int tot = total_walkers(ctx);
-    const int sms = device_sms();
-    const int target = tune_target(ctx), bias = tune_producer_bias(ctx);
     for (int c = 0; c < nc; ++c) {
-        int model, N, w, m, lw;
+        int model, N, w, m, lw, wpc, producers;
         class_shape(ctx, c, &model, &N, &w, &m, &lw);
-        if (m > 32) return 1;
-        auto producers = [&](int wpc) {
-            return forced_producers(ctx) ? forced_producers(ctx)
-                                         : std::max(1, std::min(4, pick_producers(model, wpc * m) + bias));
-        };
-        auto smem = [&](int wpc) { return sweep_smem_bytes(wpc * m, wpc, w, lw, producers(wpc), N); };
-        if (sweep_smem_bytes(m, 1, w, lw, 1, N) > 227 * 1024) return 1;
-        int wpc = forced_wpc(ctx);
-        if (!wpc) {
-            wpc = std::max(1, (target ? target : pick_walkers(tot, sms)) / m);
-            while (wpc > 1 && (wpc * m > 32 || smem(wpc) > kSmemBudget)) --wpc;
-        }
-        if (wpc * m > 32 || smem(wpc) > 227 * 1024) return 1;
-        plan_class(ctx, c, wpc, producers(wpc));
+        if (block_shape(ctx, model, N, w, m, lw, &wpc, &producers)) return 1;
+        plan_class(ctx, c, wpc, producers);
     }
     return 0;
 }

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "librewl.so")
 
 ISING, POTTS = 0, 1
 OPT_CHECK_EVERY, OPT_PRODUCER_WARPS, OPT_WINDOWS_PER_CTA, OPT_MAX_SWEEPS_PER_LAUNCH, OPT_AUTOTUNE = 1, 2, 3, 4, 5
-OPT_LATTICE_PLACEMENT = 6
+OPT_LATTICE_PLACEMENT, OPT_LNG_SHIFT = 6, 7
 STATUS = {0: "REWL_OK", -1: "REWL_EINVAL", -2: "REWL_ENOMEM", -3: "REWL_ECUDA", -4: "REWL_ETIMEOUT",
           -5: "REWL_ESTATE", -6: "REWL_EDEVICE"}
 

@@ -484,3 +484,29 @@ def test_transfer_bytes_count_every_copy():
     gpu.set_initial_lng(0, np.zeros(g["B"]), 0.5)
     h2d2, d2h2 = gpu.transfer_bytes()
     assert h2d2 - h2d1 == 2 * nbytes + 4 * g["h"] + g["h"] and d2h2 - d2h1 == 4
+
+
+SHIFTED = [
+    ("config0_full", _ising(8, 4, 1, seed=60), 1000, 200),
+    ("ising_L6_h2_m3_full", _ising(6, 2, 3, seed=61), 1000, 200),
+    ("potts_q3_L4_full", _potts(4, 3, 2, 2, seed=62), 1000, 200),
+    ("potts_q10_L200_sub", _potts(200, 10, 3, 2, seed=63, e_min=-60000, e_max=-59000), 2, 3),
+]
+
+
+@pytest.mark.parametrize("name,d,sweeps,cycles", SHIFTED, ids=[c[0] for c in SHIFTED])
+def test_lowered_windows_match_oracle(name, d, sweeps, cycles):
+    """A running window's ln g lowered by 2^s once all of it has reached 2^s
+    (s = 3 here, so it happens throughout the run): bit-exact against the
+    oracle doing the same, to full convergence on the small lattices."""
+    gpu = make_gpu([d], lng_shift=3)
+    orc = make_oracle(d)
+    orc.set_shift_exp(3)
+    orc.init()
+    for c in range(cycles):
+        step_both(gpu, [orc], sweeps)
+        if orc.all_converged():
+            break
+    assert_same_state(gpu, 0, orc, f"{name} after {c + 1} cycles")
+    if cycles > 10:
+        assert orc.all_converged() and gpu.status(0)["all_converged"]

@@ -471,3 +471,45 @@ def test_mlp_reference_gradient_matches_finite_differences():
         pm[i] -= h
         fd = (M.loss(pp, x, t) - M.loss(pm, x, t)) / (2 * h)
         assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(fd), (i, fd, g[i])
+
+
+@pytest.mark.parametrize("model,L,q,h,m", [(O.ISING, 8, 2, 4, 1), (O.ISING, 6, 2, 2, 3), (O.POTTS, 4, 3, 2, 2)])
+def test_lowering_a_window_by_a_constant_leaves_the_run_unchanged(model, L, q, h, m):
+    """ln g of a window is defined up to a constant: lowering a running
+    window's ln g by 2^s once all of it reached 2^s (here s = 3, so it happens
+    many times) must leave every decision of the run unchanged -- the same
+    configurations, energies, histograms, stages, exchanges and convergence
+    sweeps as with the default s = 20 (never reached at these sizes) -- and
+    each window's ln g must differ from the default run's by one multiple of
+    2^3 on its realisable bins, so the joined DOS is the same."""
+    N = L * L
+    runs = []
+    for s in (20, 3):
+        o = O.Oracle(model, L, q, -2 * N, 2 * N if model == O.ISING else 0, h, 0.75, m, seed=7)
+        o.set_shift_exp(s)
+        o.init()
+        for _ in range(400):
+            o.run(1000)
+            o.exchange()
+            if o.all_converged():
+                break
+        assert o.all_converged()
+        runs.append(o)
+    a, b = runs[0].state(), runs[1].state()
+    for key in ("spins", "E", "bin", "H", "stage", "conv", "latch", "replica"):
+        assert np.array_equal(a[key], b[key]), key
+    ca, cb = runs[0].counters(), runs[1].counters()
+    for key in ("ex_prop", "ex_acc", "n_acc", "conv_sweep"):
+        assert np.array_equal(ca[key], cb[key]), key
+    o = runs[0]
+    lowered = 0
+    for win in range(h):
+        rb = o.reach[o.lo[win]:o.lo[win] + o.ww[win]].astype(bool)
+        d = a["lng"][win * m:(win + 1) * m, :o.ww[win]][:, rb] - b["lng"][win * m:(win + 1) * m, :o.ww[win]][:, rb]
+        assert np.all(d == d.flat[0]) and d.flat[0] % 8 == 0, win
+        lowered += d.flat[0] > 0
+    assert lowered == h                    # every window was lowered at least once
+    bw, lf = (4.0, math.log(2)) if model == O.ISING else (1.0, math.log(q))
+    ga, _ = cc.concatenate(runs[0].pieces(), o.lo, o.w, o.reach, bw, lf)
+    gb, _ = cc.concatenate(runs[1].pieces(), o.lo, o.w, o.reach, bw, lf)
+    assert np.allclose(ga, gb, rtol=0, atol=1e-9, equal_nan=True)
