@@ -349,6 +349,28 @@ def profile_case():
     print(json.dumps({"profile_case": "config1 batch, 2 x (20 sweeps + exchange)", "sweeps": st["sweeps"]}))
 
 
+def profile_case_large():
+    """A lattice kept in global memory: one q = 10 Potts L = 400 instance
+    (windows of about 490 bins, one walker each: 2610 walkers, 418 MB of
+    lattices, more than L2), two cycles of 2 sweeps + exchange, for ncu."""
+    import torch
+    from paper_1407_5140_gb300 import rewl as R
+    from paper_1407_5140_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    ds = W.potts_fss(sizes=(400,), seeds=1, walkers=1, seed0=80000)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = R.Rewl([R.instance(**d) for d in ds], stream=stream)
+    for _ in range(2):
+        ctx.run(2)
+        ctx.exchange()
+    torch.cuda.synchronize()
+    st = ctx.status(0)
+    ctx.close()
+    print(json.dumps({"profile_case": "q=10 Potts L=400, 2610 windows x 1 walker, 2 x (2 sweeps + exchange)",
+                      "sweeps": st["sweeps"]}))
+
+
 def _golden_ising(L):
     """Exact ln g of the L x L Ising model on its bin grid, from the fixture
     written by tests/golden/make_golden.py (nan where no configuration)."""
@@ -554,7 +576,8 @@ def potts_tc_workload(exchange_interval=1000, poll_cycles=5, cap_s=1500.0):
 
 
 def potts_tc_large_workload(sizes=(32, 48, 64, 80, 100, 128), seeds=4, width=490, stage_final=20,
-                            exchange_interval=None, poll_cycles=5, cap_s=2400.0, seed0=60000, save=None):
+                            exchange_interval=None, poll_cycles=5, cap_s=2400.0, seed0=60000, save=None,
+                            e_range=None):
     """q = 10 Potts transition temperature from C_v maxima (Sec. IV A): one
     batch per lattice size (its seeds together), the batches driven
     concurrently from host threads on their own streams, so each size runs
@@ -567,7 +590,10 @@ def potts_tc_large_workload(sizes=(32, 48, 64, 80, 100, 128), seeds=4, width=490
     replacement, 200 times, each resample joined) when there are several
     seeds, and the fit Tc(L) = Tc + a / L^2 against the exact
     1 / ln(1 + sqrt q).  `save`: write every instance's pieces and geometry to
-    this .npz file (for pooling runs)."""
+    this .npz file (for pooling runs).  e_range = (a, b): energies restricted
+    to [a N, b N], which must hold the canonical weight of the temperatures
+    searched (the ground-state edge of large lattices is by far the slowest
+    part of a full-range run and carries no weight near Tc)."""
     import math
     import threading
     import numpy as np
@@ -582,7 +608,7 @@ def potts_tc_large_workload(sizes=(32, 48, 64, 80, 100, 128), seeds=4, width=490
     n_seeds = dict(zip(sizes, seeds)) if isinstance(seeds, (tuple, list)) else {L: seeds for L in sizes}
     runs = {}
     for L in sizes:
-        ds = W.potts_fss(sizes=(L,), seeds=n_seeds[L], walkers=1, seed0=seed0, width=width)
+        ds = W.potts_fss(sizes=(L,), seeds=n_seeds[L], walkers=1, seed0=seed0, width=width, e_range=e_range)
         for d in ds:
             d["ln_f_final"] = 2.0 ** -stage_final
         x = exchange_interval or max(50, int(round(1e7 / (L * L))))
@@ -669,7 +695,8 @@ def potts_tc_large_workload(sizes=(32, 48, 64, 80, 100, 128), seeds=4, width=490
     out = {"metric": "q=10 Potts transition temperature from C_v maxima", "n_gpus": 1, "data": "synthetic",
            "workload": f"q=10 Potts L={list(sizes)}, windows of ~{width} bins at 75 %, 1 walker each, "
                        f"{[n_seeds[L] for L in sizes]} seeds per size, one batch per size run concurrently, "
-                       f"ln f_final = 2^-{stage_final}",
+                       f"ln f_final = 2^-{stage_final}, energies "
+                       f"{'[-2N, 0]' if e_range is None else f'[{e_range[0]} N, {e_range[1]} N]'}",
            "seconds": secs, "walkers": int(sum(r["ds"][0]["n_windows"] * n_seeds[L] for L, r in runs.items())),
            "sizes": per, "fits": fits, "Tc_exact": tc_exact, "clocks": clk.summary()}
     print(json.dumps(out))
@@ -986,6 +1013,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-converge", action="store_true",
                     help="skip the time-to-converge runs (Config 0 and Config 2 to ln f = 2^-20)")
+    ap.add_argument("--profile-case-large", action="store_true",
+                    help="a Potts L=400 batch (lattices in global memory) with 2-sweep launches (for ncu captures)")
     ap.add_argument("--profile-case", action="store_true",
                     help="only the workload's launch shape with 20 sweeps per launch (for ncu captures)")
     ap.add_argument("--sizes", default=None, help="potts-tc-large: comma-separated lattice sides")
@@ -994,6 +1023,7 @@ def main():
     ap.add_argument("--stage-final", type=int, default=None, help="potts-tc-large: last WL stage (ln f = 2^-k)")
     ap.add_argument("--cap-s", type=float, default=None, help="potts-tc-large: wall-time cap of the run")
     ap.add_argument("--seed0", type=int, default=None, help="potts-tc-large: first seed")
+    ap.add_argument("--e-range", default=None, help="potts-tc-large: energies [a N, b N] as 'a,b'")
     ap.add_argument("--save", default=None, help="potts-tc-large: .npz file for the per-window pieces")
     ap.add_argument("--ising-only", action="store_true", help="warm-start: the Ising L=128 target only")
     ap.add_argument("--tune-at", default=None,
@@ -1009,6 +1039,9 @@ def main():
                          "balanced-windows: equal vs run-time-balanced windows; "
                          "balanced-converge: time to converge on equal vs balanced windows (Potts q=10 L=64)")
     args = ap.parse_args()
+    if args.profile_case_large:
+        profile_case_large()
+        return
     if args.profile_case:
         profile_case()
         return
@@ -1049,6 +1082,8 @@ def main():
             kw["cap_s"] = args.cap_s
         if args.seed0 is not None:
             kw["seed0"] = args.seed0
+        if args.e_range:
+            kw["e_range"] = tuple(float(x) for x in args.e_range.split(","))
         potts_tc_large_workload(save=args.save, **kw)
         return
     if args.workload == "configs":

@@ -70,16 +70,21 @@ def config4_targets():
     return [_inst(ISING, 128, 2, 64, 4, 6128), _inst(POTTS, 64, 10, 64, 4, 7064)]
 
 
-def potts_fss(sizes=(16, 24, 32, 48, 64), seeds=4, q=10, width=490, walkers=4, seed0=8000):
+def potts_fss(sizes=(16, 24, 32, 48, 64), seeds=4, q=10, width=490, walkers=4, seed0=8000, e_range=None):
     """q-state Potts instances for locating the transition from specific-heat
     maxima (Sec. IV A): windows of about `width` bins at 75 % overlap,
-    `walkers` walkers each, `seeds` independent runs per size."""
+    `walkers` walkers each, `seeds` independent runs per size.  e_range =
+    (a, b) restricts the energies to [a N, b N] (default: all, [-2N, 0])."""
     out = []
     for L in sizes:
-        B = 2 * L * L + 1
+        N = L * L
+        e_min, e_max = (-2 * N, 0) if e_range is None else (int(round(e_range[0] * N)), int(round(e_range[1] * N)))
+        B = e_max - e_min + 1
         h = max(4, int(round((B / width - 1.0) / 0.25 + 1.0)))
         for s in range(seeds):
-            out.append(_inst(POTTS, L, q, h, walkers, seed0 + 100 * L + s))
+            d = _inst(POTTS, L, q, h, walkers, seed0 + 100 * L + s)
+            d.update(e_min=e_min, e_max=e_max)
+            out.append(d)
     return out
 
 
