@@ -577,7 +577,7 @@ def potts_tc_workload(exchange_interval=1000, poll_cycles=5, cap_s=1500.0):
 
 def potts_tc_large_workload(sizes=(32, 48, 64, 80, 100, 128), seeds=4, width=490, stage_final=20,
                             exchange_interval=None, poll_cycles=5, cap_s=2400.0, seed0=60000, save=None,
-                            e_range=None):
+                            e_range=None, lattice_placement=0):
     """q = 10 Potts transition temperature from C_v maxima (Sec. IV A): one
     batch per lattice size (its seeds together), the batches driven
     concurrently from host threads on their own streams, so each size runs
@@ -619,6 +619,8 @@ def potts_tc_large_workload(sizes=(32, 48, 64, 80, 100, 128), seeds=4, width=490
         try:
             t0 = time.perf_counter()
             ctx = R.Rewl([R.instance(**d) for d in r["ds"]], stream=r["stream"])
+            if lattice_placement:
+                ctx.set_option(R.OPT_LATTICE_PLACEMENT, lattice_placement)
             ctx.run(1)
             r["stream"].synchronize()
             r["create_s"] = time.perf_counter() - t0
@@ -1024,6 +1026,8 @@ def main():
     ap.add_argument("--cap-s", type=float, default=None, help="potts-tc-large: wall-time cap of the run")
     ap.add_argument("--seed0", type=int, default=None, help="potts-tc-large: first seed")
     ap.add_argument("--e-range", default=None, help="potts-tc-large: energies [a N, b N] as 'a,b'")
+    ap.add_argument("--lattice-placement", type=int, default=0,
+                    help="potts-tc-large: 1 = lattices in global memory, 2 = shared (default: by size)")
     ap.add_argument("--save", default=None, help="potts-tc-large: .npz file for the per-window pieces")
     ap.add_argument("--ising-only", action="store_true", help="warm-start: the Ising L=128 target only")
     ap.add_argument("--tune-at", default=None,
@@ -1084,6 +1088,8 @@ def main():
             kw["seed0"] = args.seed0
         if args.e_range:
             kw["e_range"] = tuple(float(x) for x in args.e_range.split(","))
+        if args.lattice_placement:
+            kw["lattice_placement"] = args.lattice_placement
         potts_tc_large_workload(save=args.save, **kw)
         return
     if args.workload == "configs":

@@ -57,10 +57,19 @@ int block_shape(const rewl_ctx *ctx, int model, int N, int w, int m, int lw, int
     };
     auto smem = [&](int wpc) { return sweep_smem_bytes(wpc * m, wpc, w, lw, producers(wpc), N); };
     if (m > 32 || sweep_smem_bytes(m, 1, w, lw, 1, N) > 227 * 1024) return 1;
+    // shared memory per block: room for two blocks per SM, unless the whole
+    // batch at this shape has no more blocks than SMs (then one block may
+    // take all of it, so wide windows do not split a small batch into more
+    // blocks than there are SMs)
+    const long long tot = total_walkers(ctx);
+    auto fits = [&](int wpc) {
+        const long long blocks = (tot + (long long)wpc * m - 1) / ((long long)wpc * m);
+        return smem(wpc) <= (blocks <= sms ? 227 * 1024 : kSmemBudget);
+    };
     int wpc = forced_wpc(ctx);
     if (!wpc) {
-        wpc = std::max(1, (target ? target : pick_walkers(total_walkers(ctx), sms)) / m);
-        while (wpc > 1 && (wpc * m > 32 || smem(wpc) > kSmemBudget)) --wpc;
+        wpc = std::max(1, (target ? target : pick_walkers((int)tot, sms)) / m);
+        while (wpc > 1 && (wpc * m > 32 || !fits(wpc))) --wpc;
     }
     if (wpc * m > 32 || smem(wpc) > 227 * 1024) return 1;
     *wpc_out = wpc;
