@@ -47,6 +47,10 @@ def lib():
         L.oracle_all_converged.argtypes = [vp]
         L.oracle_set_check_every.argtypes = [vp, i64]
         L.oracle_set_shift_exp.argtypes = [vp, C.c_int]
+        L.oracle_pct_flat.argtypes = [C.c_uint64, C.c_uint64, C.c_int, C.c_double]
+        L.oracle_pct_flat.restype = C.c_int
+        L.oracle_average_window.argtypes = [vp, C.c_int]
+        L.oracle_average_window.restype = None
         L.oracle_set_flat_rule.argtypes = [vp, C.c_int]
         L.oracle_set_windows.argtypes = [vp, vp, vp]
         L.oracle_set_windows.restype = C.c_int
@@ -95,6 +99,11 @@ def lam_fix(k):
     out = np.zeros(k.shape, np.int64)
     lib().oracle_lam(_p(k), k.size, _p(out))
     return out
+
+
+def pct_flat(min_h, sum_h, n_reach, p):
+    """The 80 % flatness predicate as the oracle evaluates it."""
+    return bool(lib().oracle_pct_flat(min_h, sum_h, n_reach, p))
 
 
 class Oracle:
@@ -203,6 +212,11 @@ class Oracle:
         """ln g of a running window is lowered by 2^e once every realisable
         bin of every walker has reached 2^e (1 <= e <= 20; 20 by default)."""
         lib().oracle_set_shift_exp(self._o, e)
+
+    def average_window(self, win):
+        """The merge alone (Sec. II A): window win's walkers take the mean of
+        their ln g, nearest multiple of 2^-32, ties to even."""
+        lib().oracle_average_window(self._o, win)
 
     def all_converged(self):
         return bool(lib().oracle_all_converged(self._o))

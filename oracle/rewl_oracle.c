@@ -460,6 +460,13 @@ int oracle_zb_flat(uint64_t min_h, double a, int stage)
     return (double)min_h >= sqrt(ldexp(a * a, stage));
 }
 
+/* the 80 % rule (Sec. II A): min H >= p <H> over the n_reach reachable
+ * bins, as min * n_reach >= p * sum in IEEE doubles */
+int oracle_pct_flat(uint64_t min_h, uint64_t sum_h, int n_reach, double p)
+{
+    return (double)min_h * (double)n_reach >= p * (double)sum_h;
+}
+
 /* flatness test (Sec. II A): no H(E) below p times the mean of H over the
  * reachable bins of the walker's window (or the Zhou-Bhatt minimum) */
 static int walker_flat(const rewl_oracle *o, int k)
@@ -473,7 +480,7 @@ static int walker_flat(const rewl_oracle *o, int k)
         sum += H[b];
     }
     if (o->flat_rule == 1) return oracle_zb_flat(mn, o->p_flat, o->stage[win]);
-    return (double)mn * (double)o->n_reach[win] >= o->p_flat * (double)sum;
+    return oracle_pct_flat(mn, sum, o->n_reach[win], o->p_flat);
 }
 
 /* nearest integer to num/den, ties to even (den > 0) */
@@ -483,6 +490,23 @@ static int64_t div_round_even(int64_t num, int64_t den)
     if (r < 0) { r += den; q -= 1; }          /* floor division */
     if (2 * r > den || (2 * r == den && (q & 1))) q += 1;
     return q;
+}
+
+/* the merge (Sec. II A): every walker of the window takes the mean of the
+ * m walkers' ln g, bin by bin, rounded to the nearest multiple of 2^-32 with
+ * ties to even */
+void oracle_average_window(rewl_oracle *o, int win)
+{
+    int m = o->m;
+    for (int b = 0; b < o->ww[win]; ++b) {
+        int64_t units = 0;
+        for (int j = 0; j < m; ++j) {
+            double v = o->lng[(size_t)(win * m + j) * o->w + b];
+            units += (int64_t)(v * 4294967296.0);   /* exact: v on the 2^-32 grid */
+        }
+        double mean = (double)div_round_even(units, m) / 4294967296.0;
+        for (int j = 0; j < m; ++j) o->lng[(size_t)(win * m + j) * o->w + b] = mean;
+    }
 }
 
 /* end-of-sweep bookkeeping for one window: latch flat walkers; when all m
@@ -511,15 +535,7 @@ static void window_boundary(rewl_oracle *o, int win)
         all &= o->latch[k];
     }
     if (!all) return;
-    for (int b = 0; b < o->ww[win]; ++b) {
-        int64_t units = 0;
-        for (int j = 0; j < m; ++j) {
-            double v = o->lng[(size_t)(win * m + j) * o->w + b];
-            units += (int64_t)(v * 4294967296.0);   /* exact: v on the 2^-32 grid */
-        }
-        double mean = (double)div_round_even(units, m) / 4294967296.0;
-        for (int j = 0; j < m; ++j) o->lng[(size_t)(win * m + j) * o->w + b] = mean;
-    }
+    oracle_average_window(o, win);
     for (int j = 0; j < m; ++j) {
         int k = win * m + j;
         memset(o->H + (size_t)k * o->w, 0, sizeof(uint64_t) * o->w);

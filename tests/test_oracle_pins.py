@@ -513,3 +513,53 @@ def test_lowering_a_window_by_a_constant_leaves_the_run_unchanged(model, L, q, h
     ga, _ = cc.concatenate(runs[0].pieces(), o.lo, o.w, o.reach, bw, lf)
     gb, _ = cc.concatenate(runs[1].pieces(), o.lo, o.w, o.reach, bw, lf)
     assert np.allclose(ga, gb, rtol=0, atol=1e-9, equal_nan=True)
+
+
+@pytest.mark.parametrize("m,sums", [
+    (2, [3, 5, -3, -5, 7, 1, -1, 2 ** 53 + 1]),
+    (3, [1, 2, -1, -2, 4, 5, -4, -5]),
+    (4, [2, 6, 10, -2, -6, -10, 3, 5]),
+])
+def test_merge_rounds_the_mean_to_nearest_ties_to_even(m, sums):
+    """The merge (Sec. II A) sets every walker of the window to the mean of
+    their ln g, on the 2^-32 grid: nearest multiple, exact halves to the even
+    one (Python's round of the exact fraction is that rule)."""
+    from fractions import Fraction
+    o = O.Oracle(O.ISING, 4, 2, -32, 32, 1, 0.75, m, seed=3)
+    o.init()
+    w = o.w
+    rows = np.zeros((m, w), np.int64)
+    for b, total in enumerate(sums):
+        # split the sum unevenly over the walkers (all on the 2^-32 grid)
+        part = [total // m + (j - m // 2) * 7 for j in range(m)]
+        part[-1] += total - sum(part)
+        rows[:, b] = part
+    for j in range(m):
+        o.set_walker_lng(j, rows[j].astype(np.float64) * 2.0 ** -32)
+    o.average_window(0)
+    got = o.state()["lng"]
+    for b, total in enumerate(sums):
+        want = round(Fraction(total, m))
+        for j in range(m):
+            assert got[j, b] * 2.0 ** 32 == want, (m, total, got[j, b] * 2.0 ** 32, want)
+
+
+def test_eighty_percent_rule_is_min_at_least_four_fifths_of_the_mean_inclusive():
+    """flat iff min H >= 0.8 <H> over the n reachable bins (Sec. II A), exact
+    80 % counting as flat: the oracle's IEEE evaluation agrees with exact
+    rational arithmetic on random cases and on constructed boundaries."""
+    rng = np.random.default_rng(5)
+    cases = []
+    for _ in range(20000):
+        n = int(rng.integers(1, 5000))
+        mean = int(rng.integers(1, 10 ** 7))
+        s = mean * n + int(rng.integers(0, n))
+        cases.append((int(rng.integers(0, 2 * mean)), s, n))
+    for _ in range(5000):                  # exactly 80 %: 5 min n = 4 sum
+        n = int(rng.integers(1, 5000))
+        k = int(rng.integers(1, 10 ** 8))
+        s = 5 * k * n                       # sum with 4 sum / (5 n) = 4 k
+        cases += [(4 * k, s, n), (4 * k - 1, s, n)]
+    for mn, s, n in cases:
+        exact = 5 * mn * n >= 4 * s
+        assert O.pct_flat(mn, s, n, 0.8) == exact, (mn, s, n)
