@@ -33,6 +33,10 @@
  *  - Work is enqueued on the stream given at creation (NULL: a stream the
  *    library creates).  rewl_run / rewl_exchange return once the work is
  *    enqueued; read-out calls synchronise.
+ *  - Distinct contexts may be driven from different host threads at the same
+ *    time (each has its own device memory, streams and CUDA graph, captured
+ *    in thread-local mode); one context must not be used by two threads at
+ *    once.
  */
 #ifndef REWL_H
 #define REWL_H
