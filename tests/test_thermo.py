@@ -136,3 +136,21 @@ def test_bootstrap_dos_matches_the_spread_of_independent_experiments():
     # an observable's error follows too
     val, err = obs["lnZ(T=3)"]
     assert err > 0 and np.isfinite(val)
+
+
+@pytest.mark.parametrize("dE", [2800.0, 28000.0, 112000.0])
+def test_cv_peak_resolves_narrow_first_order_peaks(dE):
+    """At a first-order transition the C_v peak of an L x L lattice is about
+    T^2 / (N de) wide (2e-5 at L = 200, 4e-6 at L = 400), far below the
+    coarse grid's spacing: a two-level system with the levels' weights equal
+    at T0 (its C(T) = dE^2 p (1 - p) / T^2 peaks within a few 1e-6 of T0)
+    must be located to 1e-8, against a dense scan of the closed form."""
+    T0 = 0.70123 + 1e-5 * (dE / 28000)
+    E = np.array([-dE, 0.0])
+    lg = np.array([0.0, dE / T0])
+    t, _ = TH.cv_peak(lg, E, 0.66, 0.76)
+    w = T0 * T0 / dE
+    Ts = np.linspace(T0 - 40 * w, T0 + 40 * w, 400001)
+    p = 1.0 / (1.0 + np.exp(-(lg[1] - lg[0] - (E[1] - E[0]) / Ts)))
+    C = dE * dE * p * (1 - p) / Ts ** 2
+    assert abs(t - Ts[np.argmax(C)]) < 1e-8
